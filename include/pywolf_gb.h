@@ -1,0 +1,147 @@
+/*
+ * pywolf_gb.h -- C ABI of the GB300 (sm_103a) library for the propagation of the 4D
+ * cross-spectral density (CSD) W(x1, y1, x2, y2; omega) of a planar, partially coherent
+ * source (PyWolf, arXiv 2203.02734).
+ *
+ * Data model (Sec. 3.1, Eqs. point, n12; the block layout of Sec. 3.1):
+ *   A CSD array (CSDA) is an N x N x N x N row-major array of complex64 (pw_c32),
+ *   element W[i1][j1][i2][j2] at offset ((i1*N + j1)*N + i2)*N + j2, sampling
+ *   W(xi1, xi2) with xi(i) = (i - N/2) d and eta(j) = (N/2 - j) d, where d is the
+ *   sampling of the current plane.  N must be even (N/2 is an index, Sec. 3.1).
+ *
+ * Pipeline (Algorithm 1): create a handle on caller-owned device buffers, describe the
+ *   source (GSM model, aperture, thin lens, arbitrary mask, or an uploaded CSDA), then
+ *   propagate (Fresnel, Eq. W_fresnel; or far field, Eq. W_farfield).  The source is
+ *   generated inside the propagation (it is never materialised on its own).  After a
+ *   propagation, the handle's current plane is the output plane; its CSDA is in dev_W and
+ *   its sampling is lambda z / (N d) (Eq. spatial_resolution).  S (Eq. defS, Algorithm 4)
+ *   and mu (Eq. defMu, Algorithm coherence) can be read for the current plane.
+ *
+ * Conventions fixed here (readings of the paper):
+ *   - point 1 carries the conjugated kernel (Eq. W_general), so its DFT has sign +1 and the
+ *     point-2 DFT sign -1 (Algorithm 2 applies the direct FFT to the point-2 slices);
+ *   - scale s = d^4 / (lambda z)^2 (Eq. C with Lambda = 1/(i lambda)) for both regimes;
+ *   - the circular aperture is inclusive, decided as integer r^2 <= (a/d)^2 in FP64.
+ *
+ * Ownership: every large buffer (the N^4 CSDA dev_W and the N^4 work buffer dev_work)
+ *   belongs to the caller and must stay valid until pw_csd_destroy.  The library allocates
+ *   only small O(N^2) tables (chirps, twiddles, GSM factors, S) per handle.
+ * Streams: all device work is enqueued on the handle's stream and is asynchronous; results
+ *   in device memory are valid once that stream has been synchronised.
+ * Errors: no call aborts, traps or prints.  Each returns a pw_status; the message of the
+ *   last failure on the calling thread is returned by pw_last_error().  Invalid arguments
+ *   are rejected on the host before any device work is enqueued.
+ */
+#ifndef PYWOLF_GB_H
+#define PYWOLF_GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pw_csd pw_csd; /* opaque handle */
+
+typedef enum pw_status {
+  PW_OK = 0,
+  PW_EINVAL = 1,      /* invalid argument (odd N, non-finite or non-positive length, ...) */
+  PW_ESIZE = 2,       /* a caller buffer is smaller than required */
+  PW_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  PW_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  PW_ESTATE = 5,      /* call not valid in the handle's current state */
+  PW_EUNSUPPORTED = 6 /* valid request that this build has no kernel plan for (e.g. this N) */
+} pw_status;
+
+typedef struct pw_c32 { float re, im; } pw_c32; /* layout-compatible with complex64 */
+
+/* Human-readable text of the last failure on the calling thread ("" if none).  The
+ * pointer stays valid until the next pw_* call on this thread. */
+const char* pw_last_error(void);
+
+/* Name of a status code ("PW_OK", ...). */
+const char* pw_status_string(pw_status s);
+
+/* 1 if this build has a propagation plan for grid size N, else 0. */
+int pw_supported_n(int N);
+
+/* Bytes required for each of dev_W and dev_work: N^4 * sizeof(pw_c32). */
+size_t pw_csda_bytes(int N);
+
+/* Create a handle for an N x N x N x N CSDA on the current CUDA device.
+ *   N         even, >= 2, with pw_supported_n(N) == 1
+ *   dxi_m     sampling d of the source plane in metres (finite, > 0)           (Eq. point)
+ *   lambda_m  wavelength in metres (finite, > 0); omega = 2 pi c / lambda     (Eq. q_factor)
+ *   dev_W     device buffer of >= pw_csda_bytes(N) bytes: holds an uploaded source CSDA
+ *             (pw_source_array may point here) and receives every propagated CSDA
+ *   dev_work  device buffer of >= pw_csda_bytes(N) bytes, scratch for the half-transformed
+ *             CSDA between the two passes; must not overlap dev_W
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Returns PW_EINVAL / PW_ESIZE / PW_EUNSUPPORTED for bad arguments, PW_ECUDA if the small
+ * per-handle tables cannot be allocated.  *out is NULL on failure. */
+pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m,
+                        pw_c32* dev_W, size_t W_bytes, pw_c32* dev_work, size_t work_bytes,
+                        void* stream);
+
+/* Release the handle and its small tables (synchronises the handle's stream first).
+ * Does not free dev_W / dev_work.  NULL is accepted. */
+pw_status pw_csd_destroy(pw_csd* h);
+
+/* Change the stream used by later calls. */
+pw_status pw_csd_set_stream(pw_csd* h, void* stream);
+
+/* Gaussian Schell-model source (Sec. 5.4, with the minus signs the printed exponents lost):
+ *   W0 = A exp(-(|xi1|^2 + |xi2|^2) / (4 sigma_S^2)) exp(-|xi1 - xi2|^2 / (2 sigma_mu^2)).
+ * sigma_S_m, sigma_mu_m finite > 0; amplitude finite.  Recorded only; generated inside the
+ * next propagation.  Replaces any previous source of the current plane. */
+pw_status pw_source_gsm(pw_csd* h, double sigma_S_m, double sigma_mu_m, double amplitude);
+
+/* Circular aperture Y(xi) = 1 for |xi| <= a (appendix, Eq. circle), applied as
+ * Y(xi1) W Y(xi2) at the current plane before the next propagation.  radius_m <= 0
+ * removes it.  Must be finite. */
+pw_status pw_source_aperture(pw_csd* h, double radius_m);
+
+/* Thin lens T(xi) = q*(f, xi) (Sec. 2.2), applied as T*(xi1) W T(xi2) at the current plane
+ * before the next propagation.  focal_m == 0 removes it; otherwise finite, non-zero
+ * (negative = diverging lens). */
+pw_status pw_source_lens(pw_csd* h, double focal_m);
+
+/* Arbitrary complex mask m (N x N, row-major over (i, j), device memory) applied as
+ * m*(xi1) W m(xi2) at the current plane before the next propagation (pupil, phase screen,
+ * amplitude mask; Sec. 2.2 and Sec. 5.3).  The pointer is read during the next
+ * propagation, not copied: keep it valid until then.  NULL removes it. */
+pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask);
+
+/* Use an uploaded CSDA as the source of the current plane (Sec. 3.2: a CSDA exported by a
+ * previous run or built by the user).  dev_W0 (N^4 complex64, device) may be dev_W itself.
+ * hermitian != 0 declares W0(xi2, xi1) = conj W0(xi1, xi2) (true of every CSD, Sec. 3.3), which
+ * lets the second pass store its output rows contiguously; hermitian == 0 selects the
+ * general (strided-store) second pass.  Read during the next propagation. */
+pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian);
+
+/* Fresnel propagation over distance z_m > 0 (Eq. W_fresnel; Algorithm 2 without the
+ * far-field switch).  Result: dev_W holds W at the new plane, sampling lambda z/(N d);
+ * S of the new plane is computed on the way.  Returns PW_ESTATE if no source was set. */
+pw_status pw_propagate_fresnel(pw_csd* h, double z_m);
+
+/* Far-field propagation over z_m > 0 (Eq. W_farfield: input propagators set to 1, output
+ * propagators and sampling as for Fresnel). */
+pw_status pw_propagate_farfield(pw_csd* h, double z_m);
+
+/* Sampling d of the current plane in metres. */
+pw_status pw_get_sampling(const pw_csd* h, double* d_m);
+
+/* Spectral density S[i][j] = Re W[i][j][i][j] of the current plane (Eq. defS, Algorithm 4)
+ * into dev_S (N x N float32, device). */
+pw_status pw_spectral_density(pw_csd* h, float* dev_S);
+
+/* Spectral degree of coherence mu(P1, x) = W(P1, x) / sqrt(S(P1) S(x)) of the current plane
+ * (Eq. defMu, Algorithm coherence) for P1 = (iP, jP), 0 <= iP, jP < N, into dev_mu (N x N
+ * complex64, device); mu := 0 where S(P1) S(x) <= 0. */
+pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYWOLF_GB_H */

@@ -1,0 +1,333 @@
+"""FP64 oracle: source models, Fresnel / far-field propagation, S and mu.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Plain NumPy, complex128.
+
+Notation follows the paper:
+  * a 4D cross-spectral density array (CSDA) W[i1, j1, i2, j2] samples
+    W(xi1, xi2) with xi = (xi, eta) = dxi * ((i, -j) - (N/2, -N/2))   (Sec. 3.1, Eqs. point, n12),
+    i.e. xi(i) = (i - N/2) dxi and eta(j) = (N/2 - j) dxi;
+  * the propagator is q(R, xi) = exp(i pi |xi|^2 / (lambda R))          (Eq. q_factor);
+  * the output sampling is dx = lambda R / (N dxi)                      (Eq. spatial_resolution).
+
+Readings of passages that are garbled, ambiguous or silent (each one is listed in
+the design doc with its justification):
+  R1  GSM source: W = A exp(-(|xi1|^2+|xi2|^2)/(4 sigma_S^2)) exp(-|xi1-xi2|^2/(2 sigma_mu^2))
+      (Sec. 5.4; the printed exponents lost their minus signs).
+  R2  Circular aperture: the product Y(xi1) Y(xi2) of the text (appendix), boundary
+      inclusive |xi| <= a, decided in pixel units as integer r^2 <= (a/dxi)^2 in FP64.
+  R3  DFT signs: conj kernel h* acts on point 1 (Eq. W_general) so point 1 gets
+      exp(+2 pi i X1.xi1/(lambda z)) and point 2 exp(-2 pi i X2.xi2/(lambda z));
+      Algorithm 2 applies the direct FFT to the point-2 slices and the inverse to point 1.
+  R4  Scale: secondary source with paraxial obliquity, Lambda = 1/(i lambda), so
+      C = Lambda1* Lambda2 / R^2 = 1/(lambda R)^2 (Eq. C), and the quadrature measure
+      dxi^4: s = dxi^4 / (lambda z)^2.  Far field uses the same s.
+  R5  N must be even (M = N/2 is an index, Sec. 3.1).
+  R6  mu := 0 where S(P1) S(x) <= 0 (Algorithm coherence divides by zero there).
+  R7  Centring: the DFTs act on centred indices, sum_n f[n] exp(s 2 pi i (k-N/2)(n-N/2)/N).
+  R8  GSM closed form: Eq. Wbeam is garbled; the continuous Gaussian integral is restated.
+"""
+import numpy as np
+
+__all__ = [
+    "axis_coords", "output_sampling", "q", "gsm_source", "circle_aperture", "thin_lens",
+    "apply_mask", "centred_dft2", "propagate_fft", "propagate_direct", "propagate_rows",
+    "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
+    "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters",
+]
+
+
+def _check_even(N):
+    if N < 2 or N % 2:
+        raise ValueError("N must be even and >= 2 (M = N/2 is an array index, Sec. 3.1)")
+
+
+def axis_coords(N, d):
+    """Sample positions of the centred grid, Sec. 3.1 Eqs. point and n12.
+
+    Returns (x, y) with x[i] = (i - N/2) d (first index) and y[j] = (N/2 - j) d
+    (second index); the second axis is flipped because n = (i, -j)."""
+    _check_even(N)
+    n = np.arange(N, dtype=np.float64)
+    return (n - N / 2) * d, (N / 2 - n) * d
+
+
+def output_sampling(N, dxi, lam, z):
+    """Eq. spatial_resolution with omega = 2 pi c / lambda:  dx = lambda z / (N dxi)."""
+    return lam * z / (N * dxi)
+
+
+def q(R, r2, lam):
+    """Propagator of Eq. q_factor: q(R, xi) = exp(i pi |xi|^2 / (lambda R)); r2 = |xi|^2."""
+    return np.exp(1j * np.pi * np.asarray(r2, dtype=np.float64) / (lam * R))
+
+
+def propagation_scale(dxi, lam, z):
+    """Reading R4: C dxi^4 with C = Lambda1* Lambda2 / z^2 (Eq. C) and Lambda = 1/(i lambda)."""
+    Lam = 1.0 / (1j * lam)
+    C = np.conj(Lam) * Lam / z ** 2
+    return float(np.real(C)) * dxi ** 4
+
+
+def _r2_grid(N, d):
+    x, y = axis_coords(N, d)
+    return x[:, None] ** 2 + y[None, :] ** 2
+
+
+def gsm_source(N, dxi, sigma_S, sigma_mu, A=1.0):
+    """Gaussian Schell-model CSDA, Sec. 5.4 (Eq. of W_rho4) with reading R1.
+
+    W0[i1,j1,i2,j2] = A exp(-(|xi1|^2 + |xi2|^2) / (4 sigma_S^2)) exp(-|xi1 - xi2|^2 / (2 sigma_mu^2))."""
+    x, y = axis_coords(N, dxi)
+    X1 = x[:, None, None, None]
+    Y1 = y[None, :, None, None]
+    X2 = x[None, None, :, None]
+    Y2 = y[None, None, None, :]
+    e = -((X1 ** 2 + Y1 ** 2) + (X2 ** 2 + Y2 ** 2)) / (4.0 * sigma_S ** 2)
+    e = e - ((X1 - X2) ** 2 + (Y1 - Y2) ** 2) / (2.0 * sigma_mu ** 2)
+    return (A * np.exp(e)).astype(np.complex128)
+
+
+def circle_aperture(N, dxi, radius):
+    """Circular geometry Y_c of the appendix (Eq. circle), reading R2:
+    Y = 1 where (i - N/2)^2 + (N/2 - j)^2 <= (a/dxi)^2, else 0."""
+    _check_even(N)
+    n = np.arange(N)
+    r2 = (n[:, None] - N // 2) ** 2 + (N // 2 - n[None, :]) ** 2
+    rp = radius / dxi
+    return (r2.astype(np.float64) <= rp * rp).astype(np.float64)
+
+
+def thin_lens(N, dxi, lam, f):
+    """Thin-lens transmission T = P q*(f, xi) of Sec. 2.2 with pupil P = 1."""
+    return np.conj(q(f, _r2_grid(N, dxi), lam))
+
+
+def apply_mask(W0, m):
+    """Mask applied as m*(xi1) W m(xi2)  (Sec. 2.2 T* W T; Sec. 5.3 Y* W Y)."""
+    m = np.asarray(m, dtype=np.complex128)
+    return np.conj(m)[:, :, None, None] * W0 * m[None, None, :, :]
+
+
+def centred_dft2(A, axes, sign):
+    """Unnormalised 2D DFT over `axes` on centred indices (reading R7):
+    out[k] = sum_n A[n] exp(sign 2 pi i (k - N/2)(n - N/2) / N), per axis.
+    NumPy's FFT (a library primitive) evaluates the sum; the shifts move the centre."""
+    N = A.shape[axes[0]]
+    B = np.fft.ifftshift(A, axes=axes)
+    if sign < 0:
+        B = np.fft.fft2(B, axes=axes)
+    else:
+        B = np.fft.ifft2(B, axes=axes) * (N * N)
+    return np.fft.fftshift(B, axes=axes)
+
+
+def propagate_fft(W0, dxi, lam, z, farfield=False):
+    """Algorithm 2 (freespaceprop), steps in the paper's order, FP64.
+
+    W1 = qfunction(W0)                  (Algorithm 3: W * q*(xi1) q(xi2)); skipped for far field
+    W2 = N^2 direct 2D DFTs over the point-2 pair (i2, j2)
+    W3 = transpose(W2, 2, 3, 0, 1)
+    W4 = N^2 inverse-sign (unnormalised) 2D DFTs over axes 2, 3 (= point 1)
+    W5 = transpose(W4, 2, 3, 0, 1)
+    dx = lambda z / (N dxi)             (Eq. spatial_resolution)
+    W6 = s q*(x1) q(x2) W5              (qfunction at the output grid, scale of reading R4)
+    Returns (W6, dx)."""
+    N = W0.shape[0]
+    _check_even(N)
+    W0 = np.asarray(W0, dtype=np.complex128)
+    if not farfield:
+        qin = q(z, _r2_grid(N, dxi), lam)
+        W1 = np.conj(qin)[:, :, None, None] * W0 * qin[None, None, :, :]
+    else:
+        W1 = W0.copy()
+    W2 = centred_dft2(W1, axes=(2, 3), sign=-1)
+    del W1
+    W3 = W2.transpose(2, 3, 0, 1)
+    W4 = centred_dft2(W3, axes=(2, 3), sign=+1)
+    del W2, W3
+    W5 = W4.transpose(2, 3, 0, 1)
+    dx = output_sampling(N, dxi, lam, z)
+    qout = q(z, _r2_grid(N, dx), lam)
+    W6 = propagation_scale(dxi, lam, z) * np.conj(qout)[:, :, None, None] * W5 * qout[None, None, :, :]
+    return W6, dx
+
+
+def _kernel_matrix(N, dxi, lam, z, farfield):
+    """h(X, xi) on flattened 2D point lists (row: output point X, column: source point xi).
+
+    Fresnel: h = exp(i pi |X - xi|^2 / (lambda z)), i.e. Eq. h_free with r expanded to
+    second order and Lambda/r -> Lambda/R (Eq. approx_L); the constant exp(ikz) and
+    |Lambda|/z are moved into the scale s (they cancel in h* W h up to |Lambda|^2/z^2).
+    Far field: q(xi) -> 1, so h = q(X) exp(-2 pi i X.xi / (lambda z))   (Eq. W_farfield)."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    sx = np.stack(np.meshgrid(x, y, indexing="ij"), -1).reshape(-1, 2)
+    ox = np.stack(np.meshgrid(X, Y, indexing="ij"), -1).reshape(-1, 2)
+    if farfield:
+        dot = ox @ sx.T
+        qX = q(z, (ox ** 2).sum(1), lam)
+        return qX[:, None] * np.exp(-2j * np.pi * dot / (lam * z))
+    d2 = ((ox[:, None, :] - sx[None, :, :]) ** 2).sum(-1)
+    return np.exp(1j * np.pi * d2 / (lam * z))
+
+
+def propagate_direct(W0, dxi, lam, z, farfield=False):
+    """Brute-force quadrature of Eq. W_general on the grid, O(N^8) terms:
+
+    W_B(X1, X2) = s * sum_{xi1, xi2} h*(X1, xi1) W0(xi1, xi2) h(X2, xi2),
+
+    evaluated as conj(H) @ W0 @ H^T over flattened point indices (two matmuls).
+    Independent of the chirp/DFT factorisation used by propagate_fft.  Small N only."""
+    N = W0.shape[0]
+    H = _kernel_matrix(N, dxi, lam, z, farfield)
+    Wf = np.asarray(W0, dtype=np.complex128).reshape(N * N, N * N)
+    WB = propagation_scale(dxi, lam, z) * (np.conj(H) @ Wf @ H.T)
+    return WB.reshape(N, N, N, N), output_sampling(N, dxi, lam, z)
+
+
+def propagate_rows(source_slice, N, dxi, lam, z, rows, farfield=False):
+    """Rows W_B(X1 = (i1', j1'), . ) of the propagated CSDA for large N, Eq. W_fresnel
+    with the two integrals in the printed order:
+
+      inner(X1, xi2) = sum_{xi1} q*(xi1) exp(+2 pi i X1.xi1/(lambda z)) W0(xi1, xi2)
+      W_B(X1, X2)    = s q*(X1) q(X2) sum_{xi2} inner(X1, xi2) q(xi2) exp(-2 pi i X2.xi2/(lambda z))
+
+    The point-1 sum uses the exponential directly; the point-2 sum is a centred DFT.
+    `source_slice(i1, j1)` returns W0[i1, j1, :, :] (complex128, N x N); rows is a list
+    of (i1', j1').  Returns an array (len(rows), N, N).  Cost O(N^4) per call."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    rows = list(rows)
+    inner = np.zeros((len(rows), N, N), dtype=np.complex128)
+    r2 = _r2_grid(N, dxi)
+    qin = np.ones((N, N), dtype=np.complex128) if farfield else q(z, r2, lam)
+    # c[r, i1, j1] = q*(xi1) exp(+2 pi i X1.xi1 / (lambda z))
+    c = np.empty((len(rows), N, N), dtype=np.complex128)
+    for r, (a, b) in enumerate(rows):
+        ph = (X[a] * x[:, None] + Y[b] * y[None, :]) / (lam * z)
+        c[r] = np.conj(qin) * np.exp(2j * np.pi * ph)
+    for i1 in range(N):
+        for j1 in range(N):
+            inner += c[:, i1, j1, None, None] * source_slice(i1, j1)[None]
+    inner *= qin[None]
+    out = centred_dft2(inner, axes=(1, 2), sign=-1)
+    qout = q(z, _r2_grid(N, dx), lam)
+    for r, (a, b) in enumerate(rows):
+        out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
+    return out
+
+
+def propagate_adjoint(Y, dxi, lam, z, farfield=False):
+    """Adjoint P^H of the linear map P: W0 -> W_B of propagate_fft (Hilbert-Schmidt inner
+    product <A, B> = sum conj(A) B).  P = s * D_out . F . D_in with diagonal chirp factors
+    D_in = q*(xi1) q(xi2), D_out = q*(X1) q(X2) and F = (+ sign DFT over point 1) x
+    (- sign DFT over point 2); hence P^H = s * conj(D_in) . F^H . conj(D_out), where F^H
+    flips both DFT signs (the centred DFT matrices are symmetric)."""
+    N = Y.shape[0]
+    Y = np.asarray(Y, dtype=np.complex128)
+    dx = output_sampling(N, dxi, lam, z)
+    qout = q(z, _r2_grid(N, dx), lam)
+    Y1 = qout[:, :, None, None] * Y * np.conj(qout)[None, None, :, :]
+    Y2 = centred_dft2(Y1, axes=(0, 1), sign=-1)
+    Y3 = centred_dft2(Y2, axes=(2, 3), sign=+1)
+    if not farfield:
+        qin = q(z, _r2_grid(N, dxi), lam)
+        Y3 = qin[:, :, None, None] * Y3 * np.conj(qin)[None, None, :, :]
+    return propagation_scale(dxi, lam, z) * Y3
+
+
+def spectral_density(W):
+    """Algorithm 4 (specdensity): S[i, j] = W[i, j, i, j] (complex; Re is S, Im a
+    Hermiticity residual)."""
+    N = W.shape[0]
+    i = np.arange(N)
+    return W[i[:, None], i[None, :], i[:, None], i[None, :]]
+
+
+def degree_of_coherence(W, iP, jP):
+    """Algorithm coherence with Eq. defMu: c[i, j] = W[iP, jP, i, j] / sqrt(S[i,j] S[iP,jP]),
+    S = Re W[i,j,i,j]; reading R6: c := 0 where S(P1) S(x) <= 0."""
+    S = np.real(spectral_density(W))
+    den = S * S[iP, jP]
+    out = np.zeros(S.shape, dtype=np.complex128)
+    ok = den > 0
+    out[ok] = W[iP, jP][ok] / np.sqrt(den[ok])
+    return out
+
+
+def _gsm_axis_gaussian(sigma_S, sigma_mu):
+    a = 1.0 / (2.0 * sigma_S ** 2) + 1.0 / sigma_mu ** 2
+    g = 1.0 / sigma_mu ** 2
+    return a, g
+
+
+def gsm_closed_form(N, dxi, lam, z, sigma_S, sigma_mu, A=1.0, farfield=False):
+    """Continuous-integral GSM propagation on the output grid.  The printed Eq. Wbeam of
+    Sec. 5.4 is garbled (alpha undefined), so the same integral is restated (reading R8).
+
+    Per axis, with u = (xi1, xi2):  int exp(-u^T M u / 2 + i J^T u) d^2u = 2 pi / sqrt(det M)
+    exp(-J^T M^-1 J / 2), M = [[a, -g], [-g, a]] + diag(2 pi i/(lambda z), -2 pi i/(lambda z))
+    (no diagonal term for far field), a = 1/(2 sigma_S^2) + 1/sigma_mu^2, g = 1/sigma_mu^2,
+    J = (2 pi X1/(lambda z), -2 pi X2/(lambda z)).  Each axis carries 1/(lambda z) and the
+    output propagators q*(X1) q(X2); the 4D result is A * Wx[i1', i2'] * Wy[j1', j2']."""
+    dx = output_sampling(N, dxi, lam, z)
+    X, Yc = axis_coords(N, dx)
+    a, g = _gsm_axis_gaussian(sigma_S, sigma_mu)
+    beta = 0.0 if farfield else 2.0 * np.pi / (lam * z)
+    M = np.array([[a + 1j * beta, -g], [-g, a - 1j * beta]], dtype=np.complex128)
+    detM = M[0, 0] * M[1, 1] - M[0, 1] * M[1, 0]
+    Minv = np.array([[M[1, 1], -M[0, 1]], [-M[1, 0], M[0, 0]]]) / detM
+
+    def axis(P):
+        J1 = 2 * np.pi * P[:, None] / (lam * z)
+        J2 = -2 * np.pi * P[None, :] / (lam * z)
+        quad = Minv[0, 0] * J1 * J1 + 2 * Minv[0, 1] * J1 * J2 + Minv[1, 1] * J2 * J2
+        val = (2 * np.pi / np.sqrt(detM)) * np.exp(-0.5 * quad) / (lam * z)
+        qP = q(z, P ** 2, lam)
+        return np.conj(qP)[:, None] * val * qP[None, :]
+
+    Wx = axis(X)
+    Wy = axis(Yc)
+    return A * Wx[:, None, :, None] * Wy[None, :, None, :]
+
+
+def gsm_separable_quadrature(N, dxi, lam, z, sigma_S, sigma_mu, A=1.0, farfield=False,
+                             lens_f=None):
+    """Discrete per-axis quadrature of Eq. W_general for the (separable) GSM source, optionally
+    behind a thin lens T = q*(f) (also separable): per axis an N x N matrix
+      Wx = (dxi^2/(lambda z)) conj(H) g H^T, H[X, xi] = exp(i pi (X - xi)^2/(lambda z)),
+      g[xi1, xi2] = exp(-(xi1^2 + xi2^2)/(4 sigma_S^2) - (xi1 - xi2)^2/(2 sigma_mu^2)),
+    and the 4D array A Wx[i1', i2'] Wy[j1', j2'].  Exact on the grid for any N (no FFT)."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Yc = axis_coords(N, dx)
+
+    def axis(src, out):
+        g = np.exp(-(src[:, None] ** 2 + src[None, :] ** 2) / (4 * sigma_S ** 2)
+                   - (src[:, None] - src[None, :]) ** 2 / (2 * sigma_mu ** 2)).astype(np.complex128)
+        if lens_f is not None:
+            t = np.conj(q(lens_f, src ** 2, lam))
+            g = np.conj(t)[:, None] * g * t[None, :]
+        if farfield:
+            H = q(z, out ** 2, lam)[:, None] * np.exp(-2j * np.pi * out[:, None] * src[None, :] / (lam * z))
+        else:
+            H = np.exp(1j * np.pi * (out[:, None] - src[None, :]) ** 2 / (lam * z))
+        return (dxi ** 2 / (lam * z)) * (np.conj(H) @ g @ H.T)
+
+    Wx = axis(x, X)
+    Wy = axis(y, Yc)
+    return A * Wx[:, None, :, None] * Wy[None, :, None, :]
+
+
+def gsm_beam_parameters(lam, z, sigma_S, sigma_mu):
+    """Textbook GSM beam: expansion factor Delta(z) = [1 + (z/(k sigma_S delta))^2]^(1/2),
+    1/delta^2 = 1/(4 sigma_S^2) + 1/sigma_mu^2, radius of curvature R(z) = z [1 + (k sigma_S
+    delta / z)^2] (textbook GSM beam formulas of Mandel & Wolf ch. 5, which Sec. 5.4 cites
+    for Eq. Wbeam).  Independent of gsm_closed_form; used to pin it."""
+    k = 2 * np.pi / lam
+    delta = (1.0 / (4 * sigma_S ** 2) + 1.0 / sigma_mu ** 2) ** -0.5
+    Delta = np.sqrt(1 + (z / (k * sigma_S * delta)) ** 2)
+    Rz = z * (1 + (k * sigma_S * delta / z) ** 2)
+    return Delta, Rz

@@ -1,0 +1,275 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test ties an oracle function to the paper's printed numbers, to brute force, to an
+independent closed form, or to an exact invariant, so that a dropped term, a wrong sign, a
+swapped index or a transposed operand in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")
+
+DXI, LAM, SS, SM = 20e-6, 633e-9, 0.1e-3, 0.05e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _rand_mask(N, seed):
+    u = WL.uniform01(seed, 2 * N * N).reshape(2, N, N)
+    return (u[0] + 0.2) * np.exp(2j * np.pi * u[1])
+
+
+# --------------------------------------------------------------------------- brute force
+@pytest.mark.parametrize("N", [4, 6, 8])
+@pytest.mark.parametrize("farfield", [False, True])
+def test_fft_route_equals_direct_quadrature(N, farfield):
+    """Algorithm 2 route == brute-force quadrature of Eq. W_general (no chirp/DFT
+    factorisation), on a non-symmetric masked GSM source and a random CSDA."""
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM, 1.3), _rand_mask(N, 7))
+    a, dxa = O.propagate_fft(W0, DXI, LAM, 0.5, farfield)
+    b, dxb = O.propagate_direct(W0, DXI, LAM, 0.5, farfield)
+    assert dxa == dxb
+    assert rel(a, b) < 1e-11
+    W1 = WL.random_csd(N, seed=11, n_modes=2)
+    a, _ = O.propagate_fft(W1, DXI, LAM, 0.3, farfield)
+    b, _ = O.propagate_direct(W1, DXI, LAM, 0.3, farfield)
+    assert rel(a, b) < 1e-11
+
+
+def test_direct_quadrature_is_not_symmetric_in_points():
+    """A conjugation or point swap in the kernel must show: propagating the transposed
+    (point-swapped) source of a non-Hermitian array gives a different result."""
+    N = 4
+    rng = np.random.default_rng(3)
+    W0 = rng.standard_normal((N,) * 4) + 1j * rng.standard_normal((N,) * 4)
+    a, _ = O.propagate_direct(W0, DXI, LAM, 0.5)
+    b, _ = O.propagate_direct(W0.transpose(2, 3, 0, 1), DXI, LAM, 0.5)
+    assert rel(a, b.transpose(2, 3, 0, 1)) > 1e-2
+
+
+# --------------------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("farfield", [False, True])
+def test_gsm_closed_form_equals_fft_route(farfield):
+    """Continuous Gaussian integral == discrete route once the grid holds the beam."""
+    N = 64
+    W0 = O.gsm_source(N, DXI, SS, SM, 1.0)
+    a, _ = O.propagate_fft(W0, DXI, LAM, 0.5, farfield)
+    c = O.gsm_closed_form(N, DXI, LAM, 0.5, SS, SM, 1.0, farfield)
+    assert rel(a, c) < 1e-7
+
+
+def test_gsm_closed_form_matches_textbook_beam():
+    """Closed form vs the textbook GSM beam: S(X) = (A/Delta^2) exp(-|X|^2/(2 sigma_S^2 Delta^2)),
+    |mu| = exp(-|X1-X2|^2/(2 sigma_mu^2 Delta^2)), arg W = k(|X2|^2 - |X1|^2)/(2 R(z))."""
+    N, z, A = 64, 0.5, 1.7
+    Wc = O.gsm_closed_form(N, DXI, LAM, z, SS, SM, A, False)
+    Delta, Rz = O.gsm_beam_parameters(LAM, z, SS, SM)
+    dx = O.output_sampling(N, DXI, LAM, z)
+    X, Y = O.axis_coords(N, dx)
+    S = np.real(O.spectral_density(Wc))
+    r2 = X[:, None] ** 2 + Y[None, :] ** 2
+    S_tb = (A / Delta ** 2) * np.exp(-r2 / (2 * SS ** 2 * Delta ** 2))
+    assert rel(S, S_tb) < 1e-10
+    k = 2 * np.pi / LAM
+    for (a, b) in [(32, 32), (20, 40), (45, 30)]:
+        for (c, d) in [(32, 35), (28, 36), (40, 22)]:
+            w = Wc[a, b, c, d]
+            d2 = (X[a] - X[c]) ** 2 + (Y[b] - Y[d]) ** 2
+            mu = w / np.sqrt(S[a, b] * S[c, d])
+            assert abs(abs(mu) - np.exp(-d2 / (2 * SM ** 2 * Delta ** 2))) < 1e-10
+            ph = k * ((X[c] ** 2 + Y[d] ** 2) - (X[a] ** 2 + Y[b] ** 2)) / (2 * Rz)
+            assert abs(np.angle(mu * np.exp(-1j * ph))) < 1e-9
+
+
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("farfield", [False, True])
+@pytest.mark.parametrize("lens", [None, 0.3])
+def test_separable_quadrature_equals_fft_route(N, farfield, lens):
+    """Per-axis N x N quadrature (Kronecker) == 4D Algorithm-2 route, any N."""
+    W0 = O.gsm_source(N, DXI, SS, SM, 0.8)
+    if lens is not None:
+        W0 = O.apply_mask(W0, O.thin_lens(N, DXI, LAM, lens))
+    a, _ = O.propagate_fft(W0, DXI, LAM, 0.5, farfield)
+    b = O.gsm_separable_quadrature(N, DXI, LAM, 0.5, SS, SM, 0.8, farfield, lens_f=lens)
+    assert rel(a, b) < 1e-12
+
+
+def test_propagate_rows_equals_fft_route():
+    N = 16
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), _rand_mask(N, 5))
+    full, _ = O.propagate_fft(W0, DXI, LAM, 0.4)
+    rows = [(8, 8), (3, 11), (15, 0)]
+    got = O.propagate_rows(lambda i, j: W0[i, j], N, DXI, LAM, 0.4, rows)
+    for r, (a, b) in enumerate(rows):
+        assert rel(got[r], full[a, b]) < 1e-12
+    gotf = O.propagate_rows(lambda i, j: W0[i, j], N, DXI, LAM, 0.4, rows, farfield=True)
+    fullf, _ = O.propagate_fft(W0, DXI, LAM, 0.4, True)
+    assert rel(gotf[1], fullf[3, 11]) < 1e-12
+
+
+# --------------------------------------------------------------------------- invariants
+@pytest.mark.parametrize("farfield", [False, True])
+def test_parseval_and_trace(farfield):
+    """Power conservation with the scale of reading R4: sum|W_B|^2 dx^4 = sum|W0|^2 dxi^4 and
+    sum S_B dx^2 = sum S_0 dxi^2 (the chirps are unimodular, the DFTs unitary up to N)."""
+    N = 12
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), _rand_mask(N, 9))
+    WB, dx = O.propagate_fft(W0, DXI, LAM, 0.7, farfield)
+    assert abs(np.sum(np.abs(WB) ** 2) * dx ** 4 / (np.sum(np.abs(W0) ** 2) * DXI ** 4) - 1) < 1e-12
+    S0 = np.real(O.spectral_density(W0))
+    SB = np.real(O.spectral_density(WB))
+    assert abs(SB.sum() * dx ** 2 / (S0.sum() * DXI ** 2) - 1) < 1e-12
+
+
+def test_hermitian_and_non_negative_definite():
+    """W(x2, x1) = W*(x1, x2) (Sec. 3.3) and the non-negative definiteness constraint of Sec. 2.1,
+    for a random CSDA and its propagation."""
+    N = 6
+    W0 = WL.random_csd(N, seed=21, n_modes=4)
+    WB, _ = O.propagate_fft(W0, DXI, LAM, 0.2)
+    for W in (W0, WB):
+        M = W.reshape(N * N, N * N)
+        assert np.abs(M - M.conj().T).max() < 1e-12 * np.abs(M).max()
+        ev = np.linalg.eigvalsh((M + M.conj().T) / 2)
+        assert ev.min() > -1e-11 * ev.max()
+    assert np.linalg.matrix_rank(WB.reshape(N * N, N * N), tol=1e-9 * np.abs(WB).max()) == 4
+
+
+def test_thin_lens_cancels_input_propagator():
+    """Eq. qprop3: a lens of focal length f = z in the source plane cancels the input
+    propagators, so Fresnel with the lens equals far field without it."""
+    N = 16
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), O.circle_aperture(N, DXI, 5.5 * DXI))
+    a, _ = O.propagate_fft(O.apply_mask(W0, O.thin_lens(N, DXI, LAM, 0.3)), DXI, LAM, 0.3)
+    b, _ = O.propagate_fft(W0, DXI, LAM, 0.3, farfield=True)
+    assert rel(a, b) < 1e-13
+    c, _ = O.propagate_fft(W0, DXI, LAM, 0.3)
+    assert rel(c, b) > 1e-3
+
+
+def test_s_non_negative_and_mu_bounded():
+    N = 16
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), O.circle_aperture(N, DXI, 6 * DXI))
+    WB, _ = O.propagate_fft(W0, DXI, LAM, 0.5)
+    S = np.real(O.spectral_density(WB))
+    assert S.min() > -1e-12 * S.max()
+    mu = O.degree_of_coherence(WB, 8, 8)
+    assert np.abs(mu).max() <= 1 + 1e-12
+    assert abs(mu[8, 8] - 1) < 1e-13
+
+
+def test_coherent_source_has_unit_coherence():
+    """A rank-one CSDA phi*(x1) phi(x2) is fully coherent: |mu| = 1 wherever S > 0, before and
+    after propagation (Eq. defMu, Algorithm coherence)."""
+    N = 8
+    phi = _rand_mask(N, 31)
+    W0 = np.conj(phi)[:, :, None, None] * phi[None, None]
+    for W in (W0, O.propagate_fft(W0, DXI, LAM, 0.5)[0]):
+        mu = O.degree_of_coherence(W, 3, 5)
+        assert np.allclose(np.abs(mu), 1.0, atol=1e-12)
+    mu = O.degree_of_coherence(W0, 3, 5)
+    assert np.allclose(mu, np.conj(phi[3, 5]) * phi / (np.abs(phi[3, 5]) * np.abs(phi)), atol=1e-13)
+
+
+def test_mu_zero_where_s_vanishes():
+    N = 8
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), O.circle_aperture(N, DXI, 2 * DXI))
+    mu = O.degree_of_coherence(W0, 4, 4)
+    assert mu[0, 0] == 0 and abs(mu[4, 5] - np.exp(-DXI ** 2 / (2 * SM ** 2))) < 1e-13
+
+
+# --------------------------------------------------------------------------- source models
+def test_gsm_source_special_cases():
+    """S0(xi) = A exp(-|xi|^2/(2 sigma_S^2)); mu0 = exp(-|xi1-xi2|^2/(2 sigma_mu^2)) (Sec. 5.4)."""
+    N, A = 10, 2.5
+    W0 = O.gsm_source(N, DXI, SS, SM, A)
+    x, y = O.axis_coords(N, DXI)
+    S = np.real(O.spectral_density(W0))
+    assert np.allclose(S, A * np.exp(-(x[:, None] ** 2 + y[None, :] ** 2) / (2 * SS ** 2)), rtol=1e-14)
+    mu = O.degree_of_coherence(W0, 2, 7)
+    d2 = (x[:, None] - x[2]) ** 2 + (y[None, :] - y[7]) ** 2
+    assert np.allclose(mu, np.exp(-d2 / (2 * SM ** 2)), rtol=1e-13)
+    assert x[N // 2] == 0 and y[N // 2] == 0 and y[0] > 0 and x[0] < 0
+
+
+def test_circle_aperture_brute_force():
+    N, r = 24, 7.0
+    Y = O.circle_aperture(N, DXI, r * DXI)
+    cnt = 0
+    for i in range(N):
+        for j in range(N):
+            inside = (i - N // 2) ** 2 + (N // 2 - j) ** 2 <= r * r
+            assert Y[i, j] == (1.0 if inside else 0.0)
+            cnt += inside
+    assert cnt == int(Y.sum()) == 149  # lattice points with x^2 + y^2 <= 49
+
+
+def test_q_identities():
+    """Eqs. qprop1 - qprop3 of Sec. 2.1."""
+    R, R1, R2, beta = 0.7, 0.4, 1.3, 2.5
+    r2a, r2b = np.array([1e-6, 4e-6, 9e-7]), np.array([2e-6, 5e-6, 1e-6])
+    assert np.allclose(O.q(R, r2a / beta ** 2, LAM), O.q(beta ** 2 * R, r2a, LAM), rtol=1e-13)
+    assert np.allclose(O.q(R, r2b, LAM) * np.conj(O.q(R, r2a, LAM)), O.q(R, r2b - r2a, LAM), rtol=1e-13)
+    assert np.allclose(O.q(R1, r2a, LAM) * np.conj(O.q(R2, r2a, LAM)),
+                       O.q(R1 * R2 / (R2 - R1), r2a, LAM), rtol=1e-12)
+    assert np.allclose(O.q(R, r2a, LAM) * np.conj(O.q(R, r2a, LAM)), 1.0, rtol=1e-15)
+
+
+# --------------------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("farfield", [False, True])
+def test_adjoint_dot_product(farfield):
+    """<P X, Y> = <X, P^H Y> for the propagation map P (FP64)."""
+    N = 8
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((N,) * 4) + 1j * rng.standard_normal((N,) * 4)
+    Y = rng.standard_normal((N,) * 4) + 1j * rng.standard_normal((N,) * 4)
+    PX, _ = O.propagate_fft(X, DXI, LAM, 0.5, farfield)
+    PhY = O.propagate_adjoint(Y, DXI, LAM, 0.5, farfield)
+    lhs = np.vdot(PX, Y)
+    rhs = np.vdot(X, PhY)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# --------------------------------------------------------------------------- paper numbers
+def test_golden_paper_numbers():
+    g = json.load(open(GOLDEN))["entries"]
+    by = {e["id"]: e for e in g}
+    e = by["ex3_lens_plane_sampling"]
+    i = e["inputs"]
+    lam = 2 * math.pi * i["c"] / i["omega0"]
+    dx = O.output_sampling(i["N"], i["dxi"], lam, i["R"])
+    assert abs(dx / e["printed"]["dx"] - 1) < e["rel_tol"]
+    e = by["ex4_sampling_equals_source"]
+    i = e["inputs"]
+    lam = 2 * math.pi * i["c"] / i["omega0"]
+    assert abs(lam / e["printed"]["lambda0"] - 1) < e["rel_tol"]
+    dx = O.output_sampling(i["N"], i["dxi"], lam, i["R"])
+    assert abs(dx / e["printed"]["dx"] - 1) < e["rel_tol"]
+    e = by["ex1_dark_spot"]
+    i, p = e["inputs"], e["printed"]
+    lam = 2 * math.pi * i["c"] / i["omega0"]
+    assert abs(lam / p["lambda0"] - 1) < e["rel_tol"]
+    Na = round(math.sqrt(2 * math.pi * i["Nz"]))
+    assert Na == p["Na"]
+    assert abs(Na * i["dxi"] / p["a"] - 1) < e["rel_tol"]
+    R = i["a"] ** 2 / (2 * math.pi * lam)
+    assert abs(R / p["R1"] - 1) < e["rel_tol"]
+    assert abs(i["a"] ** 2 / (lam * p["R1"]) / p["NF"] - 1) < e["rel_tol"]
+    dx = O.output_sampling(i["Nz"], i["dxi"], lam, R)
+    assert abs(dx / i["dxi"] - p["dx_over_dxi"]) < e["rel_tol_dx_over_dxi"]
+
+
+def test_odd_n_rejected():
+    with pytest.raises(ValueError):
+        O.axis_coords(7, DXI)
