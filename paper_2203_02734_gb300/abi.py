@@ -1,0 +1,127 @@
+"""Thin ctypes binding of the C ABI in include/pywolf_gb.h (argument marshalling only).
+
+Every function has the C name and takes plain integers / device addresses; every step of
+the propagation runs in the library's CUDA kernels.  A non-PW_OK status raises PwError with
+the library's message.  There is no fallback: if libpywolf_gb.so is missing or fails to
+load, importing this module raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+PW_OK, PW_EINVAL, PW_ESIZE, PW_ECUDA, PW_ETIMEOUT, PW_ESTATE, PW_EUNSUPPORTED = range(7)
+
+if not os.path.exists(_build.LIB):
+    raise ImportError("libpywolf_gb.so is not built: run `python -c \"import __graft_entry__ as g; g.build()\"` "
+                      "or `python -m paper_2203_02734_gb300.build`")
+LIB = ctypes.CDLL(_build.LIB)
+
+_vp = ctypes.c_void_p
+_d = ctypes.c_double
+_i = ctypes.c_int
+
+# name: (restype, argtypes)
+SIGNATURES = {
+    "pw_last_error": (ctypes.c_char_p, []),
+    "pw_status_string": (ctypes.c_char_p, [_i]),
+    "pw_supported_n": (_i, [_i]),
+    "pw_csda_bytes": (ctypes.c_size_t, [_i]),
+    "pw_csd_create": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t, _vp]),
+    "pw_csd_destroy": (_i, [_vp]),
+    "pw_csd_set_stream": (_i, [_vp, _vp]),
+    "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
+    "pw_source_aperture": (_i, [_vp, _d]),
+    "pw_source_lens": (_i, [_vp, _d]),
+    "pw_source_mask": (_i, [_vp, _vp]),
+    "pw_source_array": (_i, [_vp, _vp, _i]),
+    "pw_propagate_fresnel": (_i, [_vp, _d]),
+    "pw_propagate_farfield": (_i, [_vp, _d]),
+    "pw_get_sampling": (_i, [_vp, ctypes.POINTER(_d)]),
+    "pw_spectral_density": (_i, [_vp, _vp]),
+    "pw_degree_of_coherence": (_i, [_vp, _i, _i, _vp]),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(LIB, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class PwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (LIB.pw_status_string(status).decode(), msg))
+        self.status = status
+
+
+def _check(status):
+    if status != PW_OK:
+        raise PwError(status, LIB.pw_last_error().decode())
+    return status
+
+
+def pw_last_error():
+    return LIB.pw_last_error().decode()
+
+
+def pw_supported_n(N):
+    return bool(LIB.pw_supported_n(N))
+
+
+def pw_csda_bytes(N):
+    return int(LIB.pw_csda_bytes(N))
+
+
+def pw_csd_create(N, dxi_m, lambda_m, dev_W, W_bytes, dev_work, work_bytes, stream=0):
+    h = _vp()
+    _check(LIB.pw_csd_create(ctypes.byref(h), N, dxi_m, lambda_m, dev_W, W_bytes, dev_work, work_bytes, stream))
+    return h.value
+
+
+def pw_csd_destroy(h):
+    _check(LIB.pw_csd_destroy(h))
+
+
+def pw_csd_set_stream(h, stream):
+    _check(LIB.pw_csd_set_stream(h, stream))
+
+
+def pw_source_gsm(h, sigma_S_m, sigma_mu_m, amplitude=1.0):
+    _check(LIB.pw_source_gsm(h, sigma_S_m, sigma_mu_m, amplitude))
+
+
+def pw_source_aperture(h, radius_m):
+    _check(LIB.pw_source_aperture(h, radius_m))
+
+
+def pw_source_lens(h, focal_m):
+    _check(LIB.pw_source_lens(h, focal_m))
+
+
+def pw_source_mask(h, dev_mask):
+    _check(LIB.pw_source_mask(h, dev_mask))
+
+
+def pw_source_array(h, dev_W0, hermitian=True):
+    _check(LIB.pw_source_array(h, dev_W0, 1 if hermitian else 0))
+
+
+def pw_propagate_fresnel(h, z_m):
+    _check(LIB.pw_propagate_fresnel(h, z_m))
+
+
+def pw_propagate_farfield(h, z_m):
+    _check(LIB.pw_propagate_farfield(h, z_m))
+
+
+def pw_get_sampling(h):
+    d = _d()
+    _check(LIB.pw_get_sampling(h, ctypes.byref(d)))
+    return d.value
+
+
+def pw_spectral_density(h, dev_S):
+    _check(LIB.pw_spectral_density(h, dev_S))
+
+
+def pw_degree_of_coherence(h, iP, jP, dev_mu):
+    _check(LIB.pw_degree_of_coherence(h, iP, jP, dev_mu))

@@ -1,0 +1,250 @@
+// propagate.cuh -- the two fused passes of one propagation, the FP64 table kernel and the
+// S / mu kernel.
+//
+// With index centring (x(i) = (i - N/2) d, and the same for the flipped second axis), the
+// discretised Eq. W_fresnel factorises exactly as
+//   W_B(a',b',c',d') = s conj(E(a') E(b')) E(c') E(d')
+//                        sum_{a,b} e^{+2 pi i (a a' + b b')/N}  sum_{c,d} e^{-2 pi i (c c' + d d')/N}
+//                        conj(F(a,b)) F(c,d) W0core(a,b,c,d)
+// where F(i,j) = (-1)^(i+j) exp(2 pi i (tau_i + tau_j)) Y(i,j) m(i,j) folds the input
+// propagator q(xi) (Algorithm 3), a thin lens q*(f, xi), the aperture Y and a mask m, and
+// E(i) = (-1)^i exp(2 pi i tau'_i) is the output propagator on the new grid; the
+// checkerboards carry the centring and s = d^4/(lambda z)^2.  (a,b) is point 1, (c,d) point 2.
+//
+// Pass A (one CTA per point-1 pair (a,b), contiguous slice): generate conj(F(a,b)) F(c,d)
+//   A G(a,c) G(b,d) (GSM) or read the uploaded W0 slice, run the direct 2D DFT over (c,d)
+//   in shared memory, store the slice of V once.
+// Pass B (one CTA per point-2 output pair (c',d'), strided slice): gather V(., ., c', d'),
+//   run the inverse-sign 2D DFT over (a,b), apply s and the output propagators, write S on
+//   the diagonal and store.  Because a CSD is Hermitian (Sec. 3.3), the column
+//   W_B(., ., c', d') is stored conjugated as the contiguous row W_B(c', d', ., .); the
+//   general (non-Hermitian) variant stores the column in place.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace pw {
+
+__device__ __forceinline__ double frac_turns(double t) { return t - rint(t); }
+
+// exp(2 pi i t) from turns t, reduced to [-1/2, 1/2] in FP64 before sincospi.
+__device__ __forceinline__ float2 cis_turns(double t) {
+  double s, c;
+  sincospi(2.0 * frac_turns(t), &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+struct TableArgs {
+  int N;
+  double Kin;     // turns per n^2 of the point-2 input factor (propagator and lens)
+  double K0;      // turns per n^2 of the lens alone (source-plane view, no propagator)
+  double Kout;    // turns per n^2 of the output propagator
+  double gs, gm;  // GSM: d^2/(4 sigma_S^2) and d^2/(2 sigma_mu^2)
+  double ap_thr;  // aperture: n_i^2 + n_j^2 <= ap_thr (pixels^2), < 0 = none
+  const float2* mask;  // user mask (N x N) or nullptr
+  float2* F;      // N x N input factor
+  float2* M0;     // N x N source-plane mask Y * lens * m (or nullptr)
+  float* G;       // N x N GSM axis factor (or nullptr)
+  float2* tw;     // N twiddles exp(-2 pi i m / N)
+  float2* Eout;   // N output factors
+};
+
+__global__ void tables_kernel(TableArgs t) {
+  const int N = t.N, M = N / 2;
+  const int NN = N * N;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += gridDim.x * blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    const double ni = (double)(i - M), nj = (double)(j - M);
+    const double n2i = ni * ni, n2j = nj * nj;
+    const bool inside = t.ap_thr < 0.0 || (n2i + n2j) <= t.ap_thr;
+    float2 m = t.mask ? t.mask[idx] : make_float2(1.f, 0.f);
+    if (!inside) m = make_float2(0.f, 0.f);
+    const double turns = frac_turns(n2i * t.Kin) + frac_turns(n2j * t.Kin) + 0.5 * ((i + j) & 1);
+    t.F[idx] = cmul(cis_turns(turns), m);
+    if (t.M0) t.M0[idx] = cmul(cis_turns(frac_turns(n2i * t.K0) + frac_turns(n2j * t.K0)), m);
+    if (t.G) {
+      const double dij = (double)(i - j);
+      t.G[idx] = (float)exp(-(n2i + n2j) * t.gs - dij * dij * t.gm);
+    }
+    if (idx < N) {
+      const double nk = (double)(idx - M);
+      t.tw[idx] = cis_turns(-(double)idx / (double)N);
+      t.Eout[idx] = cis_turns(frac_turns(nk * nk * t.Kout) + 0.5 * (idx & 1));
+    }
+  }
+}
+
+struct PassAArgs {
+  const float2* F;
+  const float* G;
+  const float2* tw;
+  const float2* W0;  // uploaded source (ARRAY) or nullptr
+  float2* V;
+  float A;
+};
+
+template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
+
+template <int N> __host__ __device__ constexpr size_t pass_a_smem() {
+  return (size_t)N * pitch<N>() * sizeof(float2) + N * sizeof(float2) + 2 * N * sizeof(float);
+}
+template <int N> __host__ __device__ constexpr size_t pass_b_smem() {
+  return (size_t)N * pitch<N>() * sizeof(float2) + 2 * N * sizeof(float2);
+}
+
+// In-place shared-memory stages I..IEND-1 along AXIS (0: along the second index, element
+// (line, pos) at line*P + pos; 1: along the first index, element (pos, line) at pos*P + line).
+template <int N, int SIGN, int AXIS, int I, int IEND>
+__device__ __forceinline__ void smem_stages(float2* buf, const float2* tw) {
+  if constexpr (I < IEND) {
+    constexpr int P = pitch<N>(), NT = Plan<N>::NT;
+    constexpr int R = StageInfo<N, I>::R, NS = StageInfo<N, I>::NS;
+    auto ld = [buf](int line, int pos) { return AXIS == 0 ? buf[line * P + pos] : buf[pos * P + line]; };
+    auto st = [buf](int line, int pos, float2 v) {
+      if (AXIS == 0) buf[line * P + pos] = v; else buf[pos * P + line] = v;
+    };
+    fft_stage<N, R, NS, SIGN, false, NT, true>(tw, ld, st);
+    __syncthreads();
+    smem_stages<N, SIGN, AXIS, I + 1, IEND>(buf, tw);
+  }
+}
+
+template <int N, bool ARRAY>
+__global__ void __launch_bounds__(Plan<N>::NT) pass_a_kernel(PassAArgs p) {
+  constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  float2* tw = buf + N * P;
+  float* gA = reinterpret_cast<float*>(tw + N);
+  float* gB = gA + N;
+  const int ab = blockIdx.x;
+  const int a = ab / N, b = ab - a * N;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = p.tw[i];
+    if (!ARRAY) {
+      gA[i] = p.G[a * N + i];
+      gB[i] = p.G[b * N + i];
+    }
+  }
+  __syncthreads();
+  float2 s_ab = cconj(__ldg(p.F + ab));
+  if (!ARRAY) s_ab = cscale(s_ab, p.A);
+  const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+  const float2* F = p.F;
+  // Axis 1 (along c, line = d): the first stage builds the source on the fly.
+  auto gen = [&](int d, int c) -> float2 {
+    const float2 f = __ldg(F + c * N + d);
+    if (ARRAY) return cmul(cmul(s_ab, __ldg(W0 + c * N + d)), f);
+    return cscale(cmul(s_ab, f), gA[c] * gB[d]);
+  };
+  auto st1 = [buf](int d, int c, float2 v) { buf[c * P + d] = v; };
+  fft_stage<N, StageInfo<N, 0>::R, 1, -1, false, NT, false>(tw, gen, st1);
+  __syncthreads();
+  smem_stages<N, -1, 1, 1, S>(buf, tw);
+  // Axis 0 (along d, line = c); the last stage streams the slice out, lanes along d.
+  smem_stages<N, -1, 0, 0, S - 1>(buf, tw);
+  float2* Vrow = p.V + (size_t)ab * N * N;
+  auto ld0 = [buf](int c, int d) { return buf[c * P + d]; };
+  auto out = [Vrow](int c, int d, float2 v) { Vrow[c * N + d] = v; };
+  fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, -1, true, NT, false>(tw, ld0, out);
+}
+
+struct PassBArgs {
+  const float2* V;
+  const float2* tw;
+  const float2* Eout;
+  float2* W;
+  float* S;
+  float scale;
+};
+
+template <int N, bool HERM>
+__global__ void __launch_bounds__(Plan<N>::NT) pass_b_kernel(PassBArgs p) {
+  constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  float2* tw = buf + N * P;
+  float2* eo = tw + N;
+  const int cd = blockIdx.x;
+  const int c = cd / N, d = cd - c * N;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = p.tw[i];
+    eo[i] = p.Eout[i];
+  }
+  __syncthreads();
+  const float2* Vcol = p.V + cd;
+  // Axis 0 (along b, line = a): the first stage gathers the strided column.
+  auto gather = [Vcol](int a, int b) { return __ldg(Vcol + (size_t)(a * N + b) * NN); };
+  auto st0 = [buf](int a, int b, float2 v) { buf[a * P + b] = v; };
+  fft_stage<N, StageInfo<N, 0>::R, 1, +1, false, NT, false>(tw, gather, st0);
+  __syncthreads();
+  smem_stages<N, +1, 0, 1, S>(buf, tw);
+  // Axis 1 (along a, line = b); the last stage applies the epilogue, lanes along b.
+  smem_stages<N, +1, 1, 0, S - 1>(buf, tw);
+  const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
+  float2* W = p.W;
+  float* Sd = p.S;
+  auto ld1 = [buf](int b, int a) { return buf[a * P + b]; };
+  auto epi = [=](int b, int a, float2 y) {
+    const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
+    if (a == c && b == d) Sd[cd] = w.x;
+    if (HERM) W[(size_t)cd * NN + a * N + b] = cconj(w);
+    else W[(size_t)(a * N + b) * NN + cd] = w;
+  };
+  fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, false, NT, false>(tw, ld1, epi);
+}
+
+// S and mu of the current plane (Eq. defS / Algorithm 4, Eq. defMu / Algorithm coherence),
+// including masks recorded for this plane (W+ = conj(M0(x1)) W M0(x2)).
+struct SMuArgs {
+  int N;
+  int mode;            // 0: GSM model, 1: CSDA in Wsrc (S from its diagonal), 2: CSDA + S in Sprop
+  const float* G;
+  float A;
+  const float2* M0;    // nullptr = no mask
+  const float2* Wsrc;
+  const float* Sprop;
+  int iP, jP;
+  float* S_out;        // nullptr = skip
+  float2* mu_out;      // nullptr = skip
+};
+
+__device__ __forceinline__ float smu_S(const SMuArgs& a, int x) {
+  const int N = a.N, i = x / N, j = x - i * N;
+  float s;
+  if (a.mode == 0) s = a.A * a.G[i * N + i] * a.G[j * N + j];
+  else if (a.mode == 2) s = a.Sprop[x];
+  else s = a.Wsrc[(size_t)x * N * N + x].x;
+  if (a.M0) {
+    const float2 m = a.M0[x];
+    s *= m.x * m.x + m.y * m.y;
+  }
+  return s;
+}
+
+__global__ void s_mu_kernel(SMuArgs a) {
+  const int N = a.N, NN = N * N;
+  const int xp = a.iP * N + a.jP;
+  const float sp = smu_S(a, xp);
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < NN; x += gridDim.x * blockDim.x) {
+    const float sx = smu_S(a, x);
+    if (a.S_out) a.S_out[x] = sx;
+    if (a.mu_out) {
+      const int i = x / N, j = x - i * N;
+      float2 w;
+      if (a.mode == 0) {
+        w = make_float2(a.A * a.G[a.iP * N + i] * a.G[a.jP * N + j], 0.f);
+      } else {
+        w = a.Wsrc[(size_t)xp * NN + x];
+      }
+      if (a.M0) w = cmul(cmul(cconj(a.M0[xp]), a.M0[x]), w);
+      const float den = sp * sx;
+      a.mu_out[x] = den > 0.f ? cscale(w, rsqrtf(den)) : make_float2(0.f, 0.f);
+    }
+  }
+}
+
+}  // namespace pw

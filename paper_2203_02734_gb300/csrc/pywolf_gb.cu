@@ -1,0 +1,411 @@
+// pywolf_gb.cu -- C ABI of include/pywolf_gb.h: handle state, argument checks, FP64 table
+// set-up and the launch sequence of one propagation (tables -> pass A -> pass B).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/pywolf_gb.h"
+#include "propagate.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+pw_status fail(pw_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+pw_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error so the next call starts clean
+  return fail(PW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3 };
+
+}  // namespace
+
+struct pw_csd {
+  int N;
+  double d;       // sampling of the current plane
+  double lambda;
+  pw_c32* W;
+  pw_c32* work;
+  cudaStream_t stream;
+  // source of the current plane
+  SourceKind kind;
+  double sigma_S, sigma_mu, A;
+  const pw_c32* W0;
+  int hermitian;
+  // masks of the current plane
+  double aperture;  // <= 0: none
+  double lens_f;    // 0: none
+  const pw_c32* mask;
+  // small device tables (one allocation)
+  void* tables;
+  float2* F;
+  float2* M0;
+  float* G;
+  float2* tw;
+  float2* Eout;
+  float* S;       // S of the last propagated plane (pass-B epilogue)
+};
+
+namespace {
+
+bool supported(int N) {
+  switch (N) {
+    case 2: case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64:
+    case 96: case 128:
+      return true;
+    default:
+      return false;
+  }
+}
+
+size_t table_bytes(int N) {
+  const size_t NN = (size_t)N * N;
+  return NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 2 + 1024;
+}
+
+template <int N, bool ARRAY>
+cudaError_t launch_a(const pw::PassAArgs& a, cudaStream_t s) {
+  constexpr size_t smem = pw::pass_a_smem<N>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(pw::pass_a_kernel<N, ARRAY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  pw::pass_a_kernel<N, ARRAY><<<N * N, pw::Plan<N>::NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, bool HERM>
+cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
+  constexpr size_t smem = pw::pass_b_smem<N>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(pw::pass_b_kernel<N, HERM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  pw::pass_b_kernel<N, HERM><<<N * N, pw::Plan<N>::NT, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_passes(bool array, bool herm, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                          cudaStream_t s) {
+  cudaError_t e = array ? launch_a<N, true>(a, s) : launch_a<N, false>(a, s);
+  if (e != cudaSuccess) return e;
+  return herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+}
+
+cudaError_t dispatch(int N, bool array, bool herm, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                     cudaStream_t s) {
+  switch (N) {
+#define PW_CASE(NN) \
+  case NN:          \
+    return launch_passes<NN>(array, herm, a, b, s);
+    PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
+    PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128)
+#undef PW_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// Fill F, M0, G, tw, Eout for a propagation over z (z <= 0: source-plane view only).
+pw_status build_tables(pw_csd* h, double z, bool farfield) {
+  const int N = h->N;
+  const double d = h->d, lam = h->lambda;
+  pw::TableArgs t{};
+  t.N = N;
+  const double invf = h->lens_f != 0.0 ? 1.0 / h->lens_f : 0.0;
+  const double base = d * d / (2.0 * lam);
+  t.K0 = -base * invf;
+  if (z > 0.0) {
+    t.Kin = farfield ? -base * invf : base * (1.0 / z - invf);
+    const double dx = lam * z / (N * d);
+    t.Kout = dx * dx / (2.0 * lam * z);
+  }
+  if (h->kind == SRC_GSM) {
+    t.gs = d * d / (4.0 * h->sigma_S * h->sigma_S);
+    t.gm = d * d / (2.0 * h->sigma_mu * h->sigma_mu);
+    t.G = h->G;
+  }
+  if (h->aperture > 0.0) {
+    const double rp = h->aperture / d;
+    t.ap_thr = rp * rp;
+  } else {
+    t.ap_thr = -1.0;
+  }
+  t.mask = reinterpret_cast<const float2*>(h->mask);
+  t.F = h->F;
+  t.M0 = h->M0;
+  t.tw = h->tw;
+  t.Eout = h->Eout;
+  const int NN = N * N;
+  const int threads = 256;
+  const int blocks = (NN + threads - 1) / threads;
+  pw::tables_kernel<<<blocks, threads, 0, h->stream>>>(t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "table kernel launch");
+  return PW_OK;
+}
+
+bool has_masks(const pw_csd* h) { return h->aperture > 0.0 || h->lens_f != 0.0 || h->mask != nullptr; }
+
+pw_status propagate(pw_csd* h, double z, bool farfield) {
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
+  if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
+  pw_status st = build_tables(h, z, farfield);
+  if (st != PW_OK) return st;
+  const bool array = h->kind != SRC_GSM;
+  pw::PassAArgs a{};
+  a.F = h->F;
+  a.G = h->G;
+  a.tw = h->tw;
+  a.W0 = array ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
+  a.V = reinterpret_cast<float2*>(h->work);
+  a.A = (float)h->A;
+  pw::PassBArgs b{};
+  b.V = a.V;
+  b.tw = h->tw;
+  b.Eout = h->Eout;
+  b.W = reinterpret_cast<float2*>(h->W);
+  b.S = h->S;
+  const double lz = h->lambda * z;
+  b.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
+  const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
+  cudaError_t e = dispatch(h->N, array, herm, a, b, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
+  // The output plane becomes the current plane; its CSDA is in W, its masks are unset.
+  h->d = lz / (h->N * h->d);
+  h->kind = SRC_PROPAGATED;
+  h->hermitian = herm ? 1 : 0;
+  h->W0 = nullptr;
+  h->aperture = 0.0;
+  h->lens_f = 0.0;
+  h->mask = nullptr;
+  return PW_OK;
+}
+
+pw_status s_mu(pw_csd* h, int iP, int jP, float* S, pw_c32* mu) {
+  if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
+  pw_status st = build_tables(h, 0.0, false);
+  if (st != PW_OK) return st;
+  pw::SMuArgs a{};
+  a.N = h->N;
+  a.mode = h->kind == SRC_GSM ? 0 : (h->kind == SRC_ARRAY ? 1 : 2);
+  a.G = h->G;
+  a.A = (float)h->A;
+  a.M0 = has_masks(h) ? h->M0 : nullptr;
+  a.Wsrc = reinterpret_cast<const float2*>(h->kind == SRC_ARRAY ? h->W0 : h->W);
+  a.Sprop = h->S;
+  a.iP = iP;
+  a.jP = jP;
+  a.S_out = S;
+  a.mu_out = reinterpret_cast<float2*>(mu);
+  const int NN = h->N * h->N;
+  pw::s_mu_kernel<<<(NN + 255) / 256, 256, 0, h->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "S/mu kernel launch");
+  return PW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pw_last_error(void) { return g_err.c_str(); }
+
+const char* pw_status_string(pw_status s) {
+  switch (s) {
+    case PW_OK: return "PW_OK";
+    case PW_EINVAL: return "PW_EINVAL";
+    case PW_ESIZE: return "PW_ESIZE";
+    case PW_ECUDA: return "PW_ECUDA";
+    case PW_ETIMEOUT: return "PW_ETIMEOUT";
+    case PW_ESTATE: return "PW_ESTATE";
+    case PW_EUNSUPPORTED: return "PW_EUNSUPPORTED";
+  }
+  return "PW_UNKNOWN";
+}
+
+int pw_supported_n(int N) { return supported(N) ? 1 : 0; }
+
+size_t pw_csda_bytes(int N) {
+  if (N <= 0) return 0;
+  const size_t n = (size_t)N;
+  return n * n * n * n * sizeof(pw_c32);
+}
+
+pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c32* dev_W,
+                        size_t W_bytes, pw_c32* dev_work, size_t work_bytes, void* stream) {
+  g_err.clear();
+  if (!out) return fail(PW_EINVAL, "out is null");
+  *out = nullptr;
+  if (N < 2 || (N & 1)) return fail(PW_EINVAL, "N must be even and >= 2 (got %d)", N);
+  if (!finite_pos(dxi_m)) return fail(PW_EINVAL, "sampling must be finite and > 0 (got %g)", dxi_m);
+  if (!finite_pos(lambda_m)) return fail(PW_EINVAL, "wavelength must be finite and > 0 (got %g)", lambda_m);
+  if (!dev_W || !dev_work) return fail(PW_EINVAL, "dev_W and dev_work must be non-null");
+  const size_t need = pw_csda_bytes(N);
+  if (W_bytes < need || work_bytes < need)
+    return fail(PW_ESIZE, "buffers need %zu bytes each (got W %zu, work %zu)", need, W_bytes, work_bytes);
+  {
+    const char* a0 = reinterpret_cast<const char*>(dev_W);
+    const char* b0 = reinterpret_cast<const char*>(dev_work);
+    if (a0 < b0 + need && b0 < a0 + need) return fail(PW_EINVAL, "dev_W and dev_work overlap");
+  }
+  if (!supported(N)) return fail(PW_EUNSUPPORTED, "no propagation plan for N = %d in this build", N);
+  pw_csd* h = new pw_csd{};
+  h->N = N;
+  h->d = dxi_m;
+  h->lambda = lambda_m;
+  h->W = dev_W;
+  h->work = dev_work;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->kind = SRC_NONE;
+  h->A = 1.0;
+  cudaError_t e = cudaMalloc(&h->tables, table_bytes(N));
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaMalloc of the handle tables");
+  }
+  const size_t NN = (size_t)N * N;
+  char* p = reinterpret_cast<char*>(h->tables);
+  h->F = reinterpret_cast<float2*>(p);
+  p += NN * sizeof(float2);
+  h->M0 = reinterpret_cast<float2*>(p);
+  p += NN * sizeof(float2);
+  h->G = reinterpret_cast<float*>(p);
+  p += NN * sizeof(float);
+  h->S = reinterpret_cast<float*>(p);
+  p += NN * sizeof(float);
+  h->tw = reinterpret_cast<float2*>(p);
+  p += N * sizeof(float2);
+  h->Eout = reinterpret_cast<float2*>(p);
+  *out = h;
+  return PW_OK;
+}
+
+pw_status pw_csd_destroy(pw_csd* h) {
+  g_err.clear();
+  if (!h) return PW_OK;
+  cudaError_t e1 = cudaStreamSynchronize(h->stream);
+  cudaError_t e2 = cudaFree(h->tables);
+  delete h;
+  if (e1 != cudaSuccess) return cuda_fail(e1, "stream synchronize in destroy");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFree of the handle tables");
+  return PW_OK;
+}
+
+pw_status pw_csd_set_stream(pw_csd* h, void* stream) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return PW_OK;
+}
+
+pw_status pw_source_gsm(pw_csd* h, double sigma_S_m, double sigma_mu_m, double amplitude) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!finite_pos(sigma_S_m) || !finite_pos(sigma_mu_m))
+    return fail(PW_EINVAL, "sigma_S and sigma_mu must be finite and > 0 (got %g, %g)", sigma_S_m, sigma_mu_m);
+  if (!std::isfinite(amplitude)) return fail(PW_EINVAL, "amplitude must be finite");
+  h->kind = SRC_GSM;
+  h->sigma_S = sigma_S_m;
+  h->sigma_mu = sigma_mu_m;
+  h->A = amplitude;
+  h->W0 = nullptr;
+  return PW_OK;
+}
+
+pw_status pw_source_aperture(pw_csd* h, double radius_m) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!std::isfinite(radius_m)) return fail(PW_EINVAL, "aperture radius must be finite");
+  h->aperture = radius_m > 0.0 ? radius_m : 0.0;
+  return PW_OK;
+}
+
+pw_status pw_source_lens(pw_csd* h, double focal_m) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!std::isfinite(focal_m)) return fail(PW_EINVAL, "focal length must be finite");
+  h->lens_f = focal_m;
+  return PW_OK;
+}
+
+pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  h->mask = dev_mask;
+  return PW_OK;
+}
+
+pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!dev_W0) return fail(PW_EINVAL, "dev_W0 is null");
+  {
+    const size_t need = pw_csda_bytes(h->N);
+    const char* a0 = reinterpret_cast<const char*>(dev_W0);
+    const char* b0 = reinterpret_cast<const char*>(h->work);
+    if (a0 < b0 + need && b0 < a0 + need) return fail(PW_EINVAL, "dev_W0 overlaps the work buffer");
+  }
+  h->kind = SRC_ARRAY;
+  h->W0 = dev_W0;
+  h->hermitian = hermitian ? 1 : 0;
+  h->A = 1.0;
+  return PW_OK;
+}
+
+pw_status pw_propagate_fresnel(pw_csd* h, double z_m) {
+  g_err.clear();
+  return propagate(h, z_m, false);
+}
+
+pw_status pw_propagate_farfield(pw_csd* h, double z_m) {
+  g_err.clear();
+  return propagate(h, z_m, true);
+}
+
+pw_status pw_get_sampling(const pw_csd* h, double* d_m) {
+  g_err.clear();
+  if (!h || !d_m) return fail(PW_EINVAL, "null argument");
+  *d_m = h->d;
+  return PW_OK;
+}
+
+pw_status pw_spectral_density(pw_csd* h, float* dev_S) {
+  g_err.clear();
+  if (!h || !dev_S) return fail(PW_EINVAL, "null argument");
+  return s_mu(h, 0, 0, dev_S, nullptr);
+}
+
+pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu) {
+  g_err.clear();
+  if (!h || !dev_mu) return fail(PW_EINVAL, "null argument");
+  if (iP < 0 || jP < 0 || iP >= h->N || jP >= h->N)
+    return fail(PW_EINVAL, "P1 = (%d, %d) outside the %d x %d grid", iP, jP, h->N, h->N);
+  return s_mu(h, iP, jP, nullptr, dev_mu);
+}
+
+}  // extern "C"

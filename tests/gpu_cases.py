@@ -1,0 +1,96 @@
+"""Shared helpers of the GPU parity tests: run a case through the C ABI (via the torch
+convenience wrapper) and run the same case through the FP64 oracle, on identical inputs."""
+import numpy as np
+
+import oracle as O
+import workloads as WL
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def source_mask(N, dxi, lam, aperture=None, lens_f=None, mask=None):
+    """Oracle-side total mask Y * T * m (complex128), from the same rounded mask bytes."""
+    m = np.ones((N, N), dtype=np.complex128)
+    if aperture:
+        m = m * O.circle_aperture(N, dxi, aperture)
+    if lens_f:
+        m = m * O.thin_lens(N, dxi, lam, lens_f)
+    if mask is not None:
+        m = m * np.asarray(mask, dtype=np.complex64).astype(np.complex128)
+    return m
+
+
+def oracle_source(N, dxi, lam, gsm=None, array=None, aperture=None, lens_f=None, mask=None):
+    if gsm is not None:
+        W0 = O.gsm_source(N, dxi, *gsm)
+    else:
+        W0 = np.asarray(array, dtype=np.complex64).astype(np.complex128)
+    if aperture or lens_f or mask is not None:
+        W0 = O.apply_mask(W0, source_mask(N, dxi, lam, aperture, lens_f, mask))
+    return W0
+
+
+def gpu_run(N, dxi, lam, steps, gsm=None, array=None, hermitian=True, aperture=None, lens_f=None,
+            mask=None, P1=None, sync=True):
+    """steps: list of ("fresnel"|"farfield", z).  Returns dict W, S, mu, dx (numpy)."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    c = pw.CSD(N, dxi, lam)
+    keep = []
+    if gsm is not None:
+        c.source_gsm(*gsm)
+    else:
+        W0 = torch.from_numpy(WL.to_c64(array)).cuda()
+        keep.append(W0)
+        c.source_array(W0, hermitian)
+    if aperture:
+        c.source_aperture(aperture)
+    if lens_f:
+        c.source_lens(lens_f)
+    if mask is not None:
+        mt = torch.from_numpy(WL.to_c64(mask)).cuda()
+        keep.append(mt)
+        c.source_mask(mt)
+    out = {}
+    if not steps:
+        P = P1 or (N // 2, N // 2)
+        out["S"] = c.spectral_density().cpu().numpy()
+        out["mu"] = c.degree_of_coherence(*P).cpu().numpy()
+        c.close()
+        return out
+    for kind, z in steps:
+        (c.propagate_fresnel if kind == "fresnel" else c.propagate_farfield)(z)
+    P = P1 or (N // 2, N // 2)
+    S = c.spectral_density()
+    mu = c.degree_of_coherence(*P)
+    torch.cuda.synchronize()
+    out["W"] = c.W.cpu().numpy().astype(np.complex128)
+    out["S"] = S.cpu().numpy().astype(np.float64)
+    out["mu"] = mu.cpu().numpy().astype(np.complex128)
+    out["dx"] = c.sampling()
+    c.close()
+    del keep
+    return out
+
+
+def oracle_run(N, dxi, lam, steps, **src):
+    W = oracle_source(N, dxi, lam, **src)
+    d = dxi
+    for kind, z in steps:
+        W, d = O.propagate_fft(W, d, lam, z, farfield=(kind == "farfield"))
+    return W, d
+
+
+def check_s_mu(out, Wref, P1, tol=1e-5):
+    N = Wref.shape[0]
+    Sref = np.real(O.spectral_density(Wref))
+    muref = O.degree_of_coherence(Wref, *P1)
+    eS = rel(out["S"], Sref)
+    sel = Sref >= 1e-6 * Sref.max()
+    emu = rel(out["mu"][sel], muref[sel])
+    assert eS < tol, "S rel-L2 %.3e" % eS
+    assert emu < tol, "mu rel-L2 %.3e" % emu
+    assert np.abs(out["mu"]).max() <= 1 + 1e-5
+    return eS, emu
