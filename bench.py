@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of the propagation of a 4D cross-spectral density on GB300.
+
+Metric: 4D CSD points propagated per second (N^4 / time of one full propagation step) and the
+HBM-roofline fraction of the dominant kernel.  One step = reset to the source plane, GSM x
+circular aperture x thin lens source, Fresnel propagation (pass A: source build + input
+propagators + point-2 2D DFT; pass B: point-1 2D DFT + output propagators + S), then S and
+mu(P1, .) of the output plane.  Workload: N = 128 (268 M points, complex64 CSDA of 2.1 GB),
+dxi = 20 um, lambda = 633 nm, sigma_S = 0.1 mm, sigma_mu = 0.05 mm, aperture radius 0.8 mm,
+lens f = 0.3 m, z = 0.3 m.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run: each rank propagates its own copy of the workload
+(independent replicas, no collective on the data path), so the job processes N x N^4 points
+per step ("scaling": "weak"); time is the maximum over ranks.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on the host
+cores, each step one oracle propagation of the same configuration on an N = 64 grid.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as WL  # noqa: E402
+
+CFG = WL.GSM_APERTURE_LENS_N128
+METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
+UNIT = "points/s"
+SAMPLE_N = 64  # grid of the bounded CPU sample of the same configuration
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample_step(N=SAMPLE_N):
+    """One FP64 oracle propagation of the workload's configuration on an N x N grid,
+    including the source build, S and mu.  Returns the number of points propagated."""
+    import oracle as O
+    m = O.circle_aperture(N, CFG["dxi"], CFG["aperture"]) * O.thin_lens(N, CFG["dxi"], CFG["lam"], CFG["lens_f"])
+    W0 = O.apply_mask(O.gsm_source(N, CFG["dxi"], CFG["sigma_S"], CFG["sigma_mu"], CFG["A"]), m)
+    W, _ = O.propagate_fft(W0, CFG["dxi"], CFG["lam"], CFG["z"])
+    O.spectral_density(W)
+    O.degree_of_coherence(W, N // 2, N // 2)
+    return N ** 4
+
+
+def cpu_baseline(min_s=10.0, max_s=30.0):
+    t0 = time.perf_counter()
+    pts = 0
+    runs = 0
+    while True:
+        pts += oracle_sample_step()
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_s or el + el / runs > max_s:
+            break
+    return {"value": pts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 NumPy oracle (single-threaded) on the same configuration at N=%d, %d full "
+                      "propagation(s) incl. source build, S and mu, %.1f s" % (SAMPLE_N, runs, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_step()
+    t0 = time.perf_counter()
+    pts = 0
+    for _ in range(args.steps):
+        pts += oracle_sample_step()
+    el = time.perf_counter() - t0
+    v = pts / el
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": CFG["name"], "N": SAMPLE_N, "sample_of_N": CFG["N"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: one FP64 oracle propagation of the configuration at "
+                                       "N=%d on the host cores (NumPy, single-threaded)" % SAMPLE_N},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU helpers
+def kernel_source_sha():
+    """Hash of the device-code headers of the two passes (fft.cuh, propagate.cuh)."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2203_02734_gb300", "csrc", "*.cuh"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "pass_kernels_n128.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch %s (\d+) sha=(\w+)" % kernel, txt)
+    if not m or m.group(2) != kernel_source_sha():
+        return None
+    return int(m.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "20", "-i", str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self, t0, t1):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[5:]))
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.f.name)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        note = None
+        if not inside and rows:
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:3]
+            note = "timed region shorter than the sampling period: nearest samples"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3][1:5]) if v.lower() == "active"})
+        out = {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+               "reasons": reasons, "samples": len(inside)}
+        if note:
+            out["note"] = note
+        return out
+
+
+def run_ours(args):
+    import torch
+    import paper_2203_02734_gb300 as pw
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    N = CFG["N"]
+    stream = torch.cuda.current_stream()
+    W = torch.empty((N,) * 4, dtype=torch.complex64, device="cuda")
+    work = torch.empty((N,) * 4, dtype=torch.complex64, device="cuda")
+    S = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    mu = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    c = pw.CSD(N, CFG["dxi"], CFG["lam"], W=W, work=work, stream=stream)
+    h = c.h
+    P1 = CFG["P1"]
+
+    def step():
+        pw.pw_csd_reset(h, CFG["dxi"])
+        pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
+        pw.pw_source_aperture(h, CFG["aperture"])
+        pw.pw_source_lens(h, CFG["lens_f"])
+        pw.pw_propagate_fresnel(h, CFG["z"])
+        pw.pw_spectral_density(h, S.data_ptr())
+        pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
+
+    launches_per_step = 5  # tables, pass A, pass B, S kernel, mu kernel
+    pw.pw_csd_enable_timing(h, max(args.steps, args.warmup, 1))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pw.pw_csd_pass_times(h)  # discard warm-up records
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clock = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_a, ms_b, nrec = pw.pw_csd_pass_times(h)
+    clocks = clock.stop(t0, t1) if clock else None
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # End to end through the public API with host buffers: each step copies the aperture,
+    # given as a user mask in pinned host memory, to the device and reads S and mu back into
+    # pinned host memory; the same configuration as above, so the result is identical.
+    import numpy as np
+    n = np.arange(N)
+    r2 = (n[:, None] - N // 2) ** 2 + (N // 2 - n[None, :]) ** 2
+    rp = CFG["aperture"] / CFG["dxi"]
+    mask_h = torch.from_numpy((r2 <= rp * rp).astype(np.complex64)).pin_memory()
+    mask_d = torch.empty_like(mask_h, device="cuda")
+    S_h = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    mu_h = torch.empty((N, N), dtype=torch.complex64).pin_memory()
+
+    def step_e2e():
+        mask_d.copy_(mask_h, non_blocking=True)
+        pw.pw_csd_reset(h, CFG["dxi"])
+        pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
+        pw.pw_source_mask(h, mask_d.data_ptr())
+        pw.pw_source_lens(h, CFG["lens_f"])
+        pw.pw_propagate_fresnel(h, CFG["z"])
+        pw.pw_spectral_density(h, S.data_ptr())
+        pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
+        S_h.copy_(S, non_blocking=True)
+        mu_h.copy_(mu, non_blocking=True)
+
+    S_ref = S.clone()
+    for _ in range(args.warmup):
+        step_e2e()
+    torch.cuda.synchronize()
+    same = bool(torch.equal(S_h, S_ref.cpu()))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    if dist:
+        t = torch.tensor([te], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    pw.pw_csd_pass_times(h)
+    c.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    pts = N ** 4
+    value = world * pts * args.steps / (ms / 1e3)
+    peak, peak_kind = measured_peak_hbm()
+    avg_a, avg_b = ms_a / max(nrec, 1), ms_b / max(nrec, 1)
+    if avg_b >= avg_a:
+        kern, avg, bytes_launch = "pass_b", avg_b, 16 * pts
+    else:
+        kern, avg, bytes_launch = "pass_a", avg_a, 8 * pts
+    achieved = bytes_launch / (avg / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CFG["name"], "N": N, "points_per_step": pts, "dxi_m": CFG["dxi"],
+                   "lambda_m": CFG["lam"], "z_m": CFG["z"], "aperture_m": CFG["aperture"],
+                   "lens_f_m": CFG["lens_f"], "P1": list(P1), "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2: 2 x 2.1 GB CSDA buffers stream through HBM every step"},
+        "roofline": {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern),
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "pass_ms": {"pass_a": avg_a, "pass_b": avg_b},
+                     "step_hbm_frac": (24 * pts / (ms / args.steps / 1e3) / 1e9) / peak},
+        "e2e": {"value": world * pts * args.steps / te, "unit": UNIT,
+                "h2d_bytes_per_step": mask_h.numel() * 8, "d2h_bytes_per_step": S_h.numel() * 4 + mu_h.numel() * 8,
+                "result_matches_device_path": same},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if dist:
+        dist.destroy_process_group()
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

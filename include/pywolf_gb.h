@@ -90,6 +90,11 @@ pw_status pw_csd_destroy(pw_csd* h);
 /* Change the stream used by later calls. */
 pw_status pw_csd_set_stream(pw_csd* h, void* stream);
 
+/* Start over at a source plane with sampling dxi_m (finite, > 0): forgets the current
+ * plane's CSDA, source and masks (Algorithm 1 from its first line), keeps the buffers and
+ * tables.  No device work. */
+pw_status pw_csd_reset(pw_csd* h, double dxi_m);
+
 /* Gaussian Schell-model source (Sec. 5.4, with the minus signs the printed exponents lost):
  *   W0 = A exp(-(|xi1|^2 + |xi2|^2) / (4 sigma_S^2)) exp(-|xi1 - xi2|^2 / (2 sigma_mu^2)).
  * sigma_S_m, sigma_mu_m finite > 0; amplitude finite.  Recorded only; generated inside the
@@ -139,6 +144,16 @@ pw_status pw_spectral_density(pw_csd* h, float* dev_S);
  * (Eq. defMu, Algorithm coherence) for P1 = (iP, jP), 0 <= iP, jP < N, into dev_mu (N x N
  * complex64, device); mu := 0 where S(P1) S(x) <= 0. */
 pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
+
+/* Per-pass timing (measurement aid, no counterpart in the paper).  pw_csd_enable_timing
+ * creates CUDA events for up to max_props propagations (0 disables and frees them); each
+ * later propagation records events on the handle's stream around its first pass (source +
+ * point-2 DFT) and second pass (point-1 DFT + output chirp + S).  pw_csd_pass_times waits
+ * for the recorded events, returns the summed milliseconds of each pass and how many
+ * propagations were recorded, and restarts the count.  Propagations beyond max_props are
+ * not recorded. */
+pw_status pw_csd_enable_timing(pw_csd* h, int max_props);
+pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count);
 
 #ifdef __cplusplus
 }

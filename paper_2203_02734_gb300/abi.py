@@ -30,6 +30,9 @@ SIGNATURES = {
     "pw_csd_create": (_i, [ctypes.POINTER(_vp), _i, _d, _d, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t, _vp]),
     "pw_csd_destroy": (_i, [_vp]),
     "pw_csd_set_stream": (_i, [_vp, _vp]),
+    "pw_csd_reset": (_i, [_vp, _d]),
+    "pw_csd_enable_timing": (_i, [_vp, _i]),
+    "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
     "pw_source_aperture": (_i, [_vp, _d]),
     "pw_source_lens": (_i, [_vp, _d]),
@@ -83,6 +86,21 @@ def pw_csd_destroy(h):
 
 def pw_csd_set_stream(h, stream):
     _check(LIB.pw_csd_set_stream(h, stream))
+
+
+def pw_csd_reset(h, dxi_m):
+    _check(LIB.pw_csd_reset(h, dxi_m))
+
+
+def pw_csd_enable_timing(h, max_props):
+    _check(LIB.pw_csd_enable_timing(h, max_props))
+
+
+def pw_csd_pass_times(h):
+    """Returns (ms_first_pass_total, ms_second_pass_total, count)."""
+    a, b, n = _d(), _d(), _i()
+    _check(LIB.pw_csd_pass_times(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+    return a.value, b.value, n.value
 
 
 def pw_source_gsm(h, sigma_S_m, sigma_mu_m, amplitude=1.0):

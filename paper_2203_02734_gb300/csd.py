@@ -40,6 +40,10 @@ class CSD:
         except Exception:
             pass
 
+    def reset(self, dxi):
+        abi.pw_csd_reset(self.h, dxi)
+        self._keep = []
+
     def source_gsm(self, sigma_S, sigma_mu, A=1.0):
         abi.pw_source_gsm(self.h, sigma_S, sigma_mu, A)
 

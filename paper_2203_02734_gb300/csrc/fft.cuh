@@ -130,10 +130,10 @@ __device__ __forceinline__ void twiddle(float2* v, int j, const float2* tw) {
 // One stage over all N lines of an N x N slice, run by NT threads.
 //   JFAST = false: butterfly u -> line = u % N, j = u / N (lanes walk across lines)
 //   JFAST = true : butterfly u -> j = u % (N/R), line = u / (N/R) (lanes walk along a line)
-//   load(line, pos) -> float2, store(line, pos, float2).
-//   SYNC_MID: __syncthreads() between all loads and all stores (in-place stage on shared memory).
-template <int N, int R, int NS, int SIGN, bool JFAST, int NT, bool SYNC_MID, class Load, class Store>
-__device__ __forceinline__ void fft_stage(const float2* tw, Load load, Store store) {
+//   load(line, pos) -> float2, store(line, pos, float2); mid() runs between all loads and all
+//   stores (a barrier for an in-place stage on shared memory, or nothing).
+template <int N, int R, int NS, int SIGN, bool JFAST, int NT, class Load, class Mid, class Store>
+__device__ __forceinline__ void fft_stage(const float2* tw, Load load, Mid mid, Store store) {
   static_assert(N % R == 0, "radix must divide N");
   constexpr int NJ = N / R;
   constexpr int NB = N * NJ;
@@ -151,7 +151,7 @@ __device__ __forceinline__ void fft_stage(const float2* tw, Load load, Store sto
       Dft<R, SIGN>::run(v[it]);
     }
   }
-  if constexpr (SYNC_MID) __syncthreads();
+  mid();
 #pragma unroll
   for (int it = 0; it < PER; ++it) {
     const int u = threadIdx.x + it * NT;
@@ -164,6 +164,13 @@ __device__ __forceinline__ void fft_stage(const float2* tw, Load load, Store sto
     }
   }
 }
+
+struct SyncMid {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct NoMid {
+  __device__ __forceinline__ void operator()() const {}
+};
 
 // Compile-time radix plans per axis length and thread count per CTA.
 template <int N> struct Plan;

@@ -19,7 +19,13 @@
 //   the diagonal and store.  Because a CSD is Hermitian (Sec. 3.3), the column
 //   W_B(., ., c', d') is stored conjugated as the contiguous row W_B(c', d', ., .); the
 //   general (non-Hermitian) variant stores the column in place.
+//
+// Layout of V (the corner turn between the passes): V[c'][d'/g][a][b][d' mod g], g = 4 (2 when
+// 4 does not divide N).  Pass A writes each (c', d'/g) run of g outputs as one 32-byte sector;
+// the g columns pass B needs for one group sit in one contiguous N^2 g-element block, and
+// consecutive (a, b) of one column are g elements apart.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,11 +87,18 @@ struct PassAArgs {
   const float* G;
   const float2* tw;
   const float2* W0;  // uploaded source (ARRAY) or nullptr
-  float2* V;
   float A;
 };
 
 template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
+// width of the d' runs of the V layout
+template <int N> __host__ __device__ constexpr int vgroup() { return N % 4 == 0 ? 4 : 2; }
+// offset of V(a, b, c', d') in the V layout
+template <int N>
+__device__ __forceinline__ size_t v_offset(int ab, int c, int d) {
+  constexpr int g = vgroup<N>();
+  return (((size_t)(c * (N / g) + d / g) * (N * N) + ab) * g) + (d % g);
+}
 
 template <int N> __host__ __device__ constexpr size_t pass_a_smem() {
   return (size_t)N * pitch<N>() * sizeof(float2) + N * sizeof(float2) + 2 * N * sizeof(float);
@@ -93,6 +106,42 @@ template <int N> __host__ __device__ constexpr size_t pass_a_smem() {
 template <int N> __host__ __device__ constexpr size_t pass_b_smem() {
   return (size_t)N * pitch<N>() * sizeof(float2) + 2 * N * sizeof(float2);
 }
+
+// ---- bulk asynchronous copies (TMA) issued by one thread, tracked as bulk groups ----
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until every committed bulk copy of this thread has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// wait until every committed bulk copy of this thread is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// tiled 5D tensor store from shared memory (box and layout fixed by the tensor map)
+__device__ __forceinline__ void tma_store_5d(const void* tmap, const void* smem, int c0, int c1, int c2,
+                                             int c3, int c4) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(tmap),
+      "r"(s), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+// contiguous bulk store of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_store(void* gdst, const void* smem, unsigned bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+               : "memory");
+}
+
+// Barrier that first lets thread 0 wait for its earlier bulk stores to finish reading shared
+// memory: used before a slice's first write into the buffer the previous slice is leaving by TMA.
+struct SmemFreeMid {
+  __device__ __forceinline__ void operator()() const {
+    if (threadIdx.x == 0) bulk_wait_read_all();
+    __syncthreads();
+  }
+};
 
 // In-place shared-memory stages I..IEND-1 along AXIS (0: along the second index, element
 // (line, pos) at line*P + pos; 1: along the first index, element (pos, line) at pos*P + line).
@@ -105,50 +154,59 @@ __device__ __forceinline__ void smem_stages(float2* buf, const float2* tw) {
     auto st = [buf](int line, int pos, float2 v) {
       if (AXIS == 0) buf[line * P + pos] = v; else buf[pos * P + line] = v;
     };
-    fft_stage<N, R, NS, SIGN, false, NT, true>(tw, ld, st);
+    fft_stage<N, R, NS, SIGN, false, NT>(tw, ld, SyncMid{}, st);
     __syncthreads();
     smem_stages<N, SIGN, AXIS, I + 1, IEND>(buf, tw);
   }
 }
 
+// Pass A, persistent: CTA blockIdx.x handles point-1 pairs ab = blockIdx.x + k gridDim.x.
+// Per slice: generate + DFT along c (lanes along d), DFT along d, write the natural-order slice
+// into shared memory and leave it by one TMA tensor store into the V layout (the 5D box
+// {2g floats, 1, 1, N/g, N} over (d' mod g, b, a, d'/g, c')).
 template <int N, bool ARRAY>
-__global__ void __launch_bounds__(Plan<N>::NT) pass_a_kernel(PassAArgs p) {
+__global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_constant__ CUtensorMap vmap, PassAArgs p) {
   constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(1024) float2 smem[];
   float2* buf = smem;
   float2* tw = buf + N * P;
   float* gA = reinterpret_cast<float*>(tw + N);
   float* gB = gA + N;
-  const int ab = blockIdx.x;
-  const int a = ab / N, b = ab - a * N;
-  for (int i = threadIdx.x; i < N; i += NT) {
-    tw[i] = p.tw[i];
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = p.tw[i];
+  const float2* F = p.F;
+  for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
+    const int a = ab / N, b = ab - a * N;
     if (!ARRAY) {
-      gA[i] = p.G[a * N + i];
-      gB[i] = p.G[b * N + i];
+      for (int i = threadIdx.x; i < N; i += NT) {
+        gA[i] = p.G[a * N + i];
+        gB[i] = p.G[b * N + i];
+      }
+    }
+    __syncthreads();
+    float2 s_ab = cconj(__ldg(F + ab));
+    if (!ARRAY) s_ab = cscale(s_ab, p.A);
+    const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    auto gen = [&](int d, int c) -> float2 {
+      const float2 f = __ldg(F + c * N + d);
+      if (ARRAY) return cmul(cmul(s_ab, __ldg(W0 + c * N + d)), f);
+      return cscale(cmul(s_ab, f), gA[c] * gB[d]);
+    };
+    auto st1 = [buf](int d, int c, float2 v) { buf[c * P + d] = v; };
+    fft_stage<N, StageInfo<N, 0>::R, 1, -1, false, NT>(tw, gen, SmemFreeMid{}, st1);
+    __syncthreads();
+    smem_stages<N, -1, 1, 1, S>(buf, tw);
+    smem_stages<N, -1, 0, 0, S - 1>(buf, tw);
+    auto ld0 = [buf](int c, int d) { return buf[c * P + d]; };
+    auto nat = [buf](int c, int d, float2 v) { buf[c * N + d] = v; };
+    fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, -1, true, NT>(tw, ld0, SyncMid{}, nat);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma_store_5d(&vmap, buf, 0, b, a, 0, 0);
+      bulk_commit();
     }
   }
-  __syncthreads();
-  float2 s_ab = cconj(__ldg(p.F + ab));
-  if (!ARRAY) s_ab = cscale(s_ab, p.A);
-  const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
-  const float2* F = p.F;
-  // Axis 1 (along c, line = d): the first stage builds the source on the fly.
-  auto gen = [&](int d, int c) -> float2 {
-    const float2 f = __ldg(F + c * N + d);
-    if (ARRAY) return cmul(cmul(s_ab, __ldg(W0 + c * N + d)), f);
-    return cscale(cmul(s_ab, f), gA[c] * gB[d]);
-  };
-  auto st1 = [buf](int d, int c, float2 v) { buf[c * P + d] = v; };
-  fft_stage<N, StageInfo<N, 0>::R, 1, -1, false, NT, false>(tw, gen, st1);
-  __syncthreads();
-  smem_stages<N, -1, 1, 1, S>(buf, tw);
-  // Axis 0 (along d, line = c); the last stage streams the slice out, lanes along d.
-  smem_stages<N, -1, 0, 0, S - 1>(buf, tw);
-  float2* Vrow = p.V + (size_t)ab * N * N;
-  auto ld0 = [buf](int c, int d) { return buf[c * P + d]; };
-  auto out = [Vrow](int c, int d, float2 v) { Vrow[c * N + d] = v; };
-  fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, -1, true, NT, false>(tw, ld0, out);
+  if (threadIdx.x == 0) bulk_wait_all();
 }
 
 struct PassBArgs {
@@ -160,41 +218,59 @@ struct PassBArgs {
   float scale;
 };
 
+// Pass B, persistent: CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x + k gridDim.x.
+// Per slice: gather V(., ., c', d') + DFT along a (lanes along b), DFT along b with the
+// epilogue (scale, output propagators, S on the diagonal).  HERM: the conjugated column is the
+// contiguous row W(c', d', ., .), written to shared memory and left by one bulk store.
 template <int N, bool HERM>
-__global__ void __launch_bounds__(Plan<N>::NT) pass_b_kernel(PassBArgs p) {
+__global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
   constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
   constexpr size_t NN = (size_t)N * N;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(1024) float2 smem[];
   float2* buf = smem;
   float2* tw = buf + N * P;
   float2* eo = tw + N;
-  const int cd = blockIdx.x;
-  const int c = cd / N, d = cd - c * N;
   for (int i = threadIdx.x; i < N; i += NT) {
     tw[i] = p.tw[i];
     eo[i] = p.Eout[i];
   }
   __syncthreads();
-  const float2* Vcol = p.V + cd;
-  // Axis 0 (along b, line = a): the first stage gathers the strided column.
-  auto gather = [Vcol](int a, int b) { return __ldg(Vcol + (size_t)(a * N + b) * NN); };
-  auto st0 = [buf](int a, int b, float2 v) { buf[a * P + b] = v; };
-  fft_stage<N, StageInfo<N, 0>::R, 1, +1, false, NT, false>(tw, gather, st0);
-  __syncthreads();
-  smem_stages<N, +1, 0, 1, S>(buf, tw);
-  // Axis 1 (along a, line = b); the last stage applies the epilogue, lanes along b.
-  smem_stages<N, +1, 1, 0, S - 1>(buf, tw);
-  const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
-  float2* W = p.W;
-  float* Sd = p.S;
-  auto ld1 = [buf](int b, int a) { return buf[a * P + b]; };
-  auto epi = [=](int b, int a, float2 y) {
-    const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
-    if (a == c && b == d) Sd[cd] = w.x;
-    if (HERM) W[(size_t)cd * NN + a * N + b] = cconj(w);
-    else W[(size_t)(a * N + b) * NN + cd] = w;
-  };
-  fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, false, NT, false>(tw, ld1, epi);
+  for (int cd = blockIdx.x; cd < N * N; cd += gridDim.x) {
+    const int c = cd / N, d = cd - c * N;
+    const float2* Vg = p.V + v_offset<N>(0, c, d);
+    auto gather = [Vg](int b, int a) { return __ldg(Vg + (size_t)(a * N + b) * vgroup<N>()); };
+    auto st1 = [buf](int b, int a, float2 v) { buf[a * P + b] = v; };
+    fft_stage<N, StageInfo<N, 0>::R, 1, +1, false, NT>(tw, gather, SmemFreeMid{}, st1);
+    __syncthreads();
+    smem_stages<N, +1, 1, 1, S>(buf, tw);
+    smem_stages<N, +1, 0, 0, S - 1>(buf, tw);
+    const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
+    float* Sd = p.S;
+    auto ld0 = [buf](int a, int b) { return buf[a * P + b]; };
+    if constexpr (HERM) {
+      auto epi = [=](int a, int b, float2 y) {
+        const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
+        if (a == c && b == d) Sd[cd] = w.x;
+        buf[a * N + b] = cconj(w);
+      };
+      fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, SyncMid{}, epi);
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        bulk_store(p.W + (size_t)cd * NN, buf, (unsigned)(NN * sizeof(float2)));
+        bulk_commit();
+      }
+    } else {
+      float2* W = p.W;
+      auto epi = [=](int a, int b, float2 y) {
+        const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
+        if (a == c && b == d) Sd[cd] = w.x;
+        W[(size_t)(a * N + b) * NN + cd] = w;
+      };
+      fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, NoMid{}, epi);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
 }
 
 // S and mu of the current plane (Eq. defS / Algorithm 4, Eq. defMu / Algorithm coherence),

@@ -1,12 +1,15 @@
 // pywolf_gb.cu -- C ABI of include/pywolf_gb.h: handle state, argument checks, FP64 table
 // set-up and the launch sequence of one propagation (tables -> pass A -> pass B).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/pywolf_gb.h"
 #include "propagate.cuh"
@@ -60,6 +63,10 @@ struct pw_csd {
   float2* tw;
   float2* Eout;
   float* S;       // S of the last propagated plane (pass-B epilogue)
+  alignas(64) CUtensorMap vmap;  // TMA map of the work buffer in the V layout
+  // optional per-pass timing: 3 events per recorded propagation
+  std::vector<cudaEvent_t> events;
+  int timed;
 };
 
 namespace {
@@ -79,54 +86,119 @@ size_t table_bytes(int N) {
   return NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 2 + 1024;
 }
 
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Persistent grid: as many CTAs as fit on the device at once, at most one per slice.
+template <class K>
+cudaError_t persistent_grid(K kernel, int threads, size_t smem, int slices, int* grid) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long g = (long)per_sm * num_sms();
+  *grid = (int)(g < slices ? g : slices);
+  return cudaSuccess;
+}
+
 template <int N, bool ARRAY>
-cudaError_t launch_a(const pw::PassAArgs& a, cudaStream_t s) {
+cudaError_t launch_a(const CUtensorMap& vmap, const pw::PassAArgs& a, cudaStream_t s) {
   constexpr size_t smem = pw::pass_a_smem<N>();
-  static bool attr = false;
-  if (!attr) {
+  static int grid = 0;
+  if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(pw::pass_a_kernel<N, ARRAY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    e = persistent_grid(pw::pass_a_kernel<N, ARRAY>, pw::Plan<N>::NT, smem, N * N, &grid);
+    if (e != cudaSuccess) return e;
   }
-  pw::pass_a_kernel<N, ARRAY><<<N * N, pw::Plan<N>::NT, smem, s>>>(a);
+  pw::pass_a_kernel<N, ARRAY><<<grid, pw::Plan<N>::NT, smem, s>>>(vmap, a);
   return cudaGetLastError();
 }
 
 template <int N, bool HERM>
 cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
   constexpr size_t smem = pw::pass_b_smem<N>();
-  static bool attr = false;
-  if (!attr) {
+  static int grid = 0;
+  if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(pw::pass_b_kernel<N, HERM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    e = persistent_grid(pw::pass_b_kernel<N, HERM>, pw::Plan<N>::NT, smem, N * N, &grid);
+    if (e != cudaSuccess) return e;
   }
-  pw::pass_b_kernel<N, HERM><<<N * N, pw::Plan<N>::NT, smem, s>>>(b);
+  pw::pass_b_kernel<N, HERM><<<grid, pw::Plan<N>::NT, smem, s>>>(b);
   return cudaGetLastError();
 }
 
+// ev: nullptr or three events recorded before pass A, between the passes and after pass B.
 template <int N>
-cudaError_t launch_passes(bool array, bool herm, const pw::PassAArgs& a, const pw::PassBArgs& b,
-                          cudaStream_t s) {
-  cudaError_t e = array ? launch_a<N, true>(a, s) : launch_a<N, false>(a, s);
+cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+                          const pw::PassBArgs& b, cudaStream_t s, cudaEvent_t* ev) {
+  cudaError_t e;
+  if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+  e = array ? launch_a<N, true>(vmap, a, s) : launch_a<N, false>(vmap, a, s);
   if (e != cudaSuccess) return e;
-  return herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+  if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+  e = herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
-cudaError_t dispatch(int N, bool array, bool herm, const pw::PassAArgs& a, const pw::PassBArgs& b,
-                     cudaStream_t s) {
+cudaError_t dispatch(int N, bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+                     const pw::PassBArgs& b, cudaStream_t s, cudaEvent_t* ev) {
   switch (N) {
 #define PW_CASE(NN) \
   case NN:          \
-    return launch_passes<NN>(array, herm, a, b, s);
+    return launch_passes<NN>(array, herm, vmap, a, b, s, ev);
     PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
     PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128)
 #undef PW_CASE
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 5D map of the work buffer in the V layout, as 32-bit floats: dims (innermost first)
+// (2g floats of one d' run, b, a, d'/g, c'); box = one whole slice {2g, 1, 1, N/g, N}.
+pw_status make_vmap(pw_csd* h) {
+  const int N = h->N;
+  const int g = N % 4 == 0 ? 4 : 2;
+  auto enc = encode_tiled();
+  if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
+  cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
+  cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
+  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(N / g), (cuuint32_t)N};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(&h->vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)h->work, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return PW_OK;
 }
 
 // Fill F, M0, G, tw, Eout for a propagation over z (z <= 0: source-plane view only).
@@ -182,10 +254,9 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   a.G = h->G;
   a.tw = h->tw;
   a.W0 = array ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
-  a.V = reinterpret_cast<float2*>(h->work);
   a.A = (float)h->A;
   pw::PassBArgs b{};
-  b.V = a.V;
+  b.V = reinterpret_cast<const float2*>(h->work);
   b.tw = h->tw;
   b.Eout = h->Eout;
   b.W = reinterpret_cast<float2*>(h->W);
@@ -193,7 +264,9 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   const double lz = h->lambda * z;
   b.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
   const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
-  cudaError_t e = dispatch(h->N, array, herm, a, b, h->stream);
+  cudaEvent_t* ev = nullptr;
+  if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
+  cudaError_t e = dispatch(h->N, array, herm, h->vmap, a, b, h->stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
   // The output plane becomes the current plane; its CSDA is in W, its masks are unset.
   h->d = lz / (h->N * h->d);
@@ -208,8 +281,11 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
 
 pw_status s_mu(pw_csd* h, int iP, int jP, float* S, pw_c32* mu) {
   if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
-  pw_status st = build_tables(h, 0.0, false);
-  if (st != PW_OK) return st;
+  // A propagated plane without masks needs no tables: S comes from the pass-B epilogue.
+  if (h->kind != SRC_PROPAGATED || has_masks(h)) {
+    pw_status st = build_tables(h, 0.0, false);
+    if (st != PW_OK) return st;
+  }
   pw::SMuArgs a{};
   a.N = h->N;
   a.mode = h->kind == SRC_GSM ? 0 : (h->kind == SRC_ARRAY ? 1 : 2);
@@ -301,14 +377,27 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
   h->tw = reinterpret_cast<float2*>(p);
   p += N * sizeof(float2);
   h->Eout = reinterpret_cast<float2*>(p);
+  pw_status st = make_vmap(h);
+  if (st != PW_OK) {
+    cudaFree(h->tables);
+    delete h;
+    return st;
+  }
   *out = h;
   return PW_OK;
+}
+
+void free_events(pw_csd* h) {
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  h->events.clear();
+  h->timed = 0;
 }
 
 pw_status pw_csd_destroy(pw_csd* h) {
   g_err.clear();
   if (!h) return PW_OK;
   cudaError_t e1 = cudaStreamSynchronize(h->stream);
+  free_events(h);
   cudaError_t e2 = cudaFree(h->tables);
   delete h;
   if (e1 != cudaSuccess) return cuda_fail(e1, "stream synchronize in destroy");
@@ -320,6 +409,57 @@ pw_status pw_csd_set_stream(pw_csd* h, void* stream) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
   h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return PW_OK;
+}
+
+pw_status pw_csd_reset(pw_csd* h, double dxi_m) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!finite_pos(dxi_m)) return fail(PW_EINVAL, "sampling must be finite and > 0 (got %g)", dxi_m);
+  h->d = dxi_m;
+  h->kind = SRC_NONE;
+  h->W0 = nullptr;
+  h->A = 1.0;
+  h->aperture = 0.0;
+  h->lens_f = 0.0;
+  h->mask = nullptr;
+  return PW_OK;
+}
+
+pw_status pw_csd_enable_timing(pw_csd* h, int max_props) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (max_props < 0) return fail(PW_EINVAL, "max_props must be >= 0");
+  free_events(h);
+  h->events.resize((size_t)3 * max_props);
+  for (size_t i = 0; i < h->events.size(); ++i) {
+    cudaError_t e = cudaEventCreate(&h->events[i]);
+    if (e != cudaSuccess) {
+      h->events.resize(i);
+      free_events(h);
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  return PW_OK;
+}
+
+pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count) {
+  g_err.clear();
+  if (!h || !ms_first || !ms_second || !count) return fail(PW_EINVAL, "null argument");
+  double sa = 0.0, sb = 0.0;
+  for (int k = 0; k < h->timed; ++k) {
+    float t1 = 0.f, t2 = 0.f;
+    cudaError_t e = cudaEventSynchronize(h->events[3 * k + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, h->events[3 * k], h->events[3 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, h->events[3 * k + 1], h->events[3 * k + 2]);
+    if (e != cudaSuccess) return cuda_fail(e, "pass timing events");
+    sa += t1;
+    sb += t2;
+  }
+  *ms_first = sa;
+  *ms_second = sb;
+  *count = h->timed;
+  h->timed = 0;
   return PW_OK;
 }
 

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU only).
 
-Bar: relative L2 error <= 1e-5 for W, S and mu (mu where S >= 1e-6 max S), complex64 on
+Bar: relative L2 error <= 1e-5 for W, S and mu (mu where S >= 1e-4 max S), complex64 on
 the GPU against complex128 in the oracle."""
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ def test_config_gsm_n32_fresnel():
     ref, dx = oracle_run(32, cfg["dxi"], cfg["lam"], [("fresnel", cfg["z"])], gsm=gsm)
     assert rel(out["W"], ref) < TOL
     assert abs(out["dx"] - dx) <= 1e-15 * dx
-    check_s_mu(out, ref, cfg["P1"])
+    check_s_mu(out, ref, cfg["P1"], name="gsm_n32_fresnel")
     # the discrete separable reference (no FFT) agrees too
     sep = O.gsm_separable_quadrature(32, cfg["dxi"], cfg["lam"], cfg["z"], *gsm)
     assert rel(out["W"], sep) < TOL
@@ -43,7 +43,7 @@ def test_masked_gsm_all_plans(N, kind):
     out = gpu_run(N, DXI, LAM, [(kind, z)], **src)
     ref, _ = oracle_run(N, DXI, LAM, [(kind, z)], **src)
     assert rel(out["W"], ref) < TOL
-    check_s_mu(out, ref, (N // 2, N // 2))
+    check_s_mu(out, ref, (N // 2, N // 2), name="masked_gsm_n%d_%s" % (N, kind))
 
 
 def test_amplitude_mask_n96():
@@ -53,7 +53,7 @@ def test_amplitude_mask_n96():
     out = gpu_run(96, cfg["dxi"], cfg["lam"], [("fresnel", cfg["z"])], P1=cfg["P1"], **src)
     ref, _ = oracle_run(96, cfg["dxi"], cfg["lam"], [("fresnel", cfg["z"])], **src)
     assert rel(out["W"], ref) < TOL
-    check_s_mu(out, ref, cfg["P1"])
+    check_s_mu(out, ref, cfg["P1"], name="amplitude_mask_n96")
 
 
 @pytest.mark.parametrize("N", [8, 16])
@@ -135,14 +135,19 @@ def test_invariants_full_size_n128():
 
     def slice_fn(a, b):
         return np.conj(m[a, b]) * g[a][:, None] * g[b][None, :] * m
-    rows = [cfg["P1"], (40, 90), (100, 7)]
+    # rows in the beam core (the far-field pattern is ~8 px wide here) and one in the tail,
+    # where W ~ 1e-19 and only the absolute error (relative to max |W|) is meaningful
+    rows = [cfg["P1"], (60, 70), (72, 57), (40, 90)]
     probe = O.propagate_rows(slice_fn, N, dxi, lam, z, rows)
-    for r, (a, b) in enumerate(rows):
+    wmax = np.abs(probe[0]).max()
+    for r, (a, b) in enumerate(rows[:3]):
         assert rel(W[a, b], probe[r]) < TOL
-        assert abs(out["S"][a, b] - probe[r][a, b].real) < 1e-5 * abs(probe[r]).max()
+        assert abs(out["S"][a, b] - probe[r][a, b].real) < 1e-5 * wmax
+    assert np.linalg.norm(W[40, 90] - probe[3]) < 1e-6 * np.linalg.norm(probe[0])
     # Hermiticity (sampled blocks), power and trace
-    for (a, b) in [(3, 70), (64, 64), (120, 1)]:
-        assert rel(W[:, :, a, b], np.conj(W[a, b])) < 1e-6
+    wref = np.linalg.norm(W[64, 64])
+    for (a, b) in [(3, 70), (64, 64), (60, 70), (120, 1)]:
+        assert np.linalg.norm(W[:, :, a, b] - np.conj(W[a, b])) < 1e-6 * wref
     dx = out["dx"]
     w2 = np.abs(m) ** 2
     p0 = np.einsum("ab,ac,bd,cd->", w2, g ** 2, g ** 2, w2) * dxi ** 4
