@@ -140,6 +140,21 @@ def recorded_traffic(kernel):
     return int(m.group(1))
 
 
+def max_over_ranks(x, dist, device):
+    """Maximum of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, pts_per_step, steps, seconds):
+    """Whole-job points/s: every rank propagates its own workload (weak scaling)."""
+    return world * pts_per_step * steps / seconds
+
+
 class ClockSampler:
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -241,10 +256,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     ms_a, ms_b, nrec = pw.pw_csd_pass_times(h)
     clocks = clock.stop(t0, t1) if clock else None
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # End to end through the public API with host buffers: each step copies the aperture,
     # given as a user mask in pinned host memory, to the device and reads S and mu back into
@@ -283,10 +295,7 @@ def run_ours(args):
         step_e2e()
     torch.cuda.synchronize()
     te = time.perf_counter() - te0
-    if dist:
-        t = torch.tensor([te], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = max_over_ranks(te, dist, "cuda")
     pw.pw_csd_pass_times(h)
     c.close()
     if rank != 0:
@@ -295,7 +304,7 @@ def run_ours(args):
         return
 
     pts = N ** 4
-    value = world * pts * args.steps / (ms / 1e3)
+    value = job_throughput(world, pts, args.steps, ms / 1e3)
     peak, peak_kind = measured_peak_hbm()
     avg_a, avg_b = ms_a / max(nrec, 1), ms_b / max(nrec, 1)
     if avg_b >= avg_a:
@@ -316,7 +325,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "pass_ms": {"pass_a": avg_a, "pass_b": avg_b},
                      "step_hbm_frac": (24 * pts / (ms / args.steps / 1e3) / 1e9) / peak},
-        "e2e": {"value": world * pts * args.steps / te, "unit": UNIT,
+        "e2e": {"value": job_throughput(world, pts, args.steps, te), "unit": UNIT,
                 "h2d_bytes_per_step": mask_h.numel() * 8, "d2h_bytes_per_step": S_h.numel() * 4 + mu_h.numel() * 8,
                 "result_matches_device_path": same},
         "gpu_launches": launches_per_step * args.steps,
