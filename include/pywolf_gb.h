@@ -155,6 +155,35 @@ pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
 pw_status pw_csd_enable_timing(pw_csd* h, int max_props);
 pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count);
 
+/* Allocation-free Fresnel propagation of a GSM source (the paper has no counterpart).
+ * For callers that cannot allocate device memory: applications whose framework reserves all
+ * device memory in its own pool and does not let libraries call the CUDA allocator, and
+ * latency-critical loops that cannot afford the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  It computes what pw_csd_create + pw_source_gsm + pw_source_aperture
+ * + pw_source_lens + pw_source_mask + pw_propagate_fresnel + pw_spectral_density compute on a
+ * new handle, without a handle: the half-transformed CSDA and the small tables live in one
+ * fixed device array inside the library (8 MiB + 12.5 KiB, held by every device that loads the
+ * library until the process exits), so N is limited to 2 <= N <= 32 (even, pw_supported_n);
+ * larger N returns PW_EINVAL with a message naming the limit.
+ *   N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_mu_m, amplitude  as for the handle calls
+ *   aperture_m  radius of the inclusive circular aperture, <= 0 for none
+ *   lens_f_m    focal length of the thin lens in the source plane, 0 for none
+ *   dev_mask    N x N complex64 device mask applied as m*(xi1) W m(xi2), or NULL
+ *   dev_W_out   device buffer of >= N^4 * 8 bytes (W_bytes) receiving the propagated CSDA
+ *   dev_S_out   device buffer of N x N float32 receiving S of the output plane
+ *   stream      cudaStream_t (NULL = legacy default stream); work is asynchronous on it
+ * The output sampling is lambda z / (N dxi).  The first call on a device looks up the
+ * device address of the internal array (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call on a device reuses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Each call overwrites every byte of the array that it reads later, so no state is
+ * carried from one call to the next.  Allocates nothing: no cudaMalloc, no cudaFree. */
+pw_status pw_propagate_gsm_fresnel_noalloc(int N, double dxi_m, double lambda_m, double z_m,
+                                           double sigma_S_m, double sigma_mu_m, double amplitude,
+                                           double aperture_m, double lens_f_m,
+                                           const pw_c32* dev_mask, pw_c32* dev_W_out,
+                                           size_t W_bytes, float* dev_S_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,8 @@ SIGNATURES = {
     "pw_get_sampling": (_i, [_vp, ctypes.POINTER(_d)]),
     "pw_spectral_density": (_i, [_vp, _vp]),
     "pw_degree_of_coherence": (_i, [_vp, _i, _i, _vp]),
+    "pw_propagate_gsm_fresnel_noalloc": (_i, [_i, _d, _d, _d, _d, _d, _d, _d, _d, _vp, _vp, ctypes.c_size_t,
+                                             _vp, _vp]),
 }
 for _name, (_res, _args) in SIGNATURES.items():
     _f = getattr(LIB, _name)
@@ -143,3 +145,11 @@ def pw_spectral_density(h, dev_S):
 
 def pw_degree_of_coherence(h, iP, jP, dev_mu):
     _check(LIB.pw_degree_of_coherence(h, iP, jP, dev_mu))
+
+
+def pw_propagate_gsm_fresnel_noalloc(N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_mu_m, amplitude, aperture_m,
+                                     lens_f_m, dev_mask, dev_W_out, W_bytes, dev_S_out, stream=0):
+    """Allocation-free propagation (N <= 32) into caller buffers; see include/pywolf_gb.h."""
+    _check(LIB.pw_propagate_gsm_fresnel_noalloc(N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_mu_m, amplitude,
+                                                 aperture_m, lens_f_m, dev_mask, dev_W_out, W_bytes, dev_S_out,
+                                                 stream))

@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpywolf_gb.so")
 SRC = os.path.join(HERE, "csrc", "pywolf_gb.cu")
+SRCS = [SRC, os.path.join(HERE, "csrc", "noalloc.cu")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -23,7 +24,7 @@ def _nvcc():
 
 
 def _deps():
-    return [SRC] + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "pywolf_gb.h")]
+    return SRCS + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "pywolf_gb.h")]
 
 
 def up_to_date():
@@ -39,7 +40,7 @@ def build(force=False, verbose=False):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [_nvcc(), "-std=c++17", "-O3", ARCH, "-lineinfo", "-Xptxas", "-v" if verbose else "-O3",
-           "-shared", "-Xcompiler", "-fPIC", "-o", tmp, SRC]
+           "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + SRCS
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("nvcc failed (%d):\n%s\n%s" % (res.returncode, " ".join(cmd), res.stderr[-4000:]))

@@ -57,7 +57,7 @@ struct TableArgs {
   float2* Eout;   // N output factors
 };
 
-__global__ void tables_kernel(TableArgs t) {
+static __global__ void tables_kernel(TableArgs t) {
   const int N = t.N, M = N / 2;
   const int NN = N * N;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += gridDim.x * blockDim.x) {
@@ -301,7 +301,7 @@ __device__ __forceinline__ float smu_S(const SMuArgs& a, int x) {
   return s;
 }
 
-__global__ void s_mu_kernel(SMuArgs a) {
+static __global__ void s_mu_kernel(SMuArgs a) {
   const int N = a.N, NN = N * N;
   const int xp = a.iP * N + a.jP;
   const float sp = smu_S(a, xp);

@@ -39,6 +39,11 @@ enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3 }
 
 }  // namespace
 
+namespace pwi {
+// Sets the thread's message returned by pw_last_error() (used by other translation units).
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace pwi
+
 struct pw_csd {
   int N;
   double d;       // sampling of the current plane
@@ -63,7 +68,7 @@ struct pw_csd {
   float2* tw;
   float2* Eout;
   float* S;       // S of the last propagated plane (pass-B epilogue)
-  alignas(64) CUtensorMap vmap;  // TMA map of the work buffer in the V layout
+  CUtensorMap vmap;  // TMA map of the work buffer in the V layout
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
   int timed;
@@ -387,7 +392,7 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
   return PW_OK;
 }
 
-void free_events(pw_csd* h) {
+static void free_events(pw_csd* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   h->events.clear();
   h->timed = 0;
