@@ -90,6 +90,11 @@ pw_status pw_csd_destroy(pw_csd* h);
 /* Change the stream used by later calls. */
 pw_status pw_csd_set_stream(pw_csd* h, void* stream);
 
+/* Synchronise the handle's stream and report whether a bounded device-side wait gave up in
+ * any kernel since the last check (PW_ETIMEOUT: the results of that work are invalid); clears
+ * the condition.  PW_OK otherwise. */
+pw_status pw_csd_check(pw_csd* h);
+
 /* Start over at a source plane with sampling dxi_m (finite, > 0): forgets the current
  * plane's CSDA, source and masks (Algorithm 1 from its first line), keeps the buffers and
  * tables.  No device work. */

@@ -31,6 +31,7 @@ SIGNATURES = {
     "pw_csd_destroy": (_i, [_vp]),
     "pw_csd_set_stream": (_i, [_vp, _vp]),
     "pw_csd_reset": (_i, [_vp, _d]),
+    "pw_csd_check": (_i, [_vp]),
     "pw_csd_enable_timing": (_i, [_vp, _i]),
     "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
@@ -88,6 +89,10 @@ def pw_csd_destroy(h):
 
 def pw_csd_set_stream(h, stream):
     _check(LIB.pw_csd_set_stream(h, stream))
+
+
+def pw_csd_check(h):
+    _check(LIB.pw_csd_check(h))
 
 
 def pw_csd_reset(h, dxi_m):

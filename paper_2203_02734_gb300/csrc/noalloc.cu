@@ -168,7 +168,7 @@ extern "C" pw_status pw_propagate_gsm_fresnel_noalloc(int N, double dxi_m, doubl
   auto enc = encode_fn();
   if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   CUtensorMap vmap;
-  const int g = N % 4 == 0 ? 4 : 2;
+  const int g = pw::vgroup_of(N);
   const cuuint64_t run_b = (cuuint64_t)2 * g * sizeof(float);
   cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
   cuuint64_t strides[4] = {run_b, run_b * N, run_b * N * N, run_b * N * N * (N / g)};

@@ -20,10 +20,10 @@
 //   W_B(., ., c', d') is stored conjugated as the contiguous row W_B(c', d', ., .); the
 //   general (non-Hermitian) variant stores the column in place.
 //
-// Layout of V (the corner turn between the passes): V[c'][d'/g][a][b][d' mod g], g = 4 (2 when
-// 4 does not divide N).  Pass A writes each (c', d'/g) run of g outputs as one 32-byte sector;
-// the g columns pass B needs for one group sit in one contiguous N^2 g-element block, and
-// consecutive (a, b) of one column are g elements apart.
+// Layout of V (the corner turn between the passes): V[c'][d'/g][a][b][d' mod g], g = vgroup_of(N).
+// Pass A writes each (c', d'/g) run of g outputs as one piece (a 32-byte sector for g = 4); the g
+// columns of one group sit in one contiguous N^2 g-element block, and consecutive (a, b) of one
+// column are g elements apart.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -55,6 +55,7 @@ struct TableArgs {
   float* G;       // N x N GSM axis factor (or nullptr)
   float2* tw;     // N twiddles exp(-2 pi i m / N)
   float2* Eout;   // N output factors
+  float2* Ein;    // N per-axis input factors (-1)^i exp(2 pi i Kin n_i^2), or nullptr
 };
 
 static __global__ void tables_kernel(TableArgs t) {
@@ -78,6 +79,7 @@ static __global__ void tables_kernel(TableArgs t) {
       const double nk = (double)(idx - M);
       t.tw[idx] = cis_turns(-(double)idx / (double)N);
       t.Eout[idx] = cis_turns(frac_turns(nk * nk * t.Kout) + 0.5 * (idx & 1));
+      if (t.Ein) t.Ein[idx] = cis_turns(frac_turns(nk * nk * t.Kin) + 0.5 * (idx & 1));
     }
   }
 }
@@ -91,8 +93,11 @@ struct PassAArgs {
 };
 
 template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
-// width of the d' runs of the V layout
-template <int N> __host__ __device__ constexpr int vgroup() { return N % 4 == 0 ? 4 : 2; }
+// Width g of the d' runs of the V layout: 4 (one 32-byte sector per run; 2 when 4 does not
+// divide N).  Narrower 16-byte runs halve pass B's gather traffic but make pass A's TMA store
+// issue twice as many half-sector writes, which costs more than it saves (measured at N = 128).
+__host__ __device__ constexpr int vgroup_of(int n) { return n % 4 == 0 ? 4 : 2; }
+template <int N> __host__ __device__ constexpr int vgroup() { return vgroup_of(N); }
 // offset of V(a, b, c', d') in the V layout
 template <int N>
 __device__ __forceinline__ size_t v_offset(int ab, int c, int d) {

@@ -13,6 +13,7 @@
 
 #include "../../include/pywolf_gb.h"
 #include "propagate.cuh"
+#include "r128.cuh"
 
 namespace {
 
@@ -67,7 +68,9 @@ struct pw_csd {
   float* G;
   float2* tw;
   float2* Eout;
+  float2* Ein;    // per-axis input factors
   float* S;       // S of the last propagated plane (pass-B epilogue)
+  int* err;       // device flag: a bounded wait in a kernel gave up
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
@@ -88,7 +91,7 @@ bool supported(int N) {
 
 size_t table_bytes(int N) {
   const size_t NN = (size_t)N * N;
-  return NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 2 + 1024;
+  return NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 3 + 1024 + 256;
 }
 
 int num_sms() {
@@ -129,6 +132,43 @@ cudaError_t launch_a(const CUtensorMap& vmap, const pw::PassAArgs& a, cudaStream
   return cudaGetLastError();
 }
 
+// N = 128: register-resident pass A (r128.cuh).
+struct R128Extra {
+  const float2* Ein;
+  const float2* mask;
+  int ap_ithr;
+  int* err;
+};
+
+template <bool ARRAY, bool MASK>
+cudaError_t launch_a_r128(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
+  constexpr size_t smem = pw::r128::pass_a_smem();
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_a_r128<ARRAY, MASK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(pw::r128::pass_a_r128<ARRAY, MASK>, pw::r128::NT, smem, 128 * 128, &grid);
+    if (e != cudaSuccess) return e;
+  }
+  pw::r128::pass_a_r128<ARRAY, MASK><<<grid, pw::r128::NT, smem, s>>>(vmap, a, x.Ein, x.mask, x.ap_ithr);
+  return cudaGetLastError();
+}
+
+// N = 128, Hermitian store: register-resident pass B with prefetched gather (r128.cuh).
+cudaError_t launch_b_r128(const pw::PassBArgs& b, cudaStream_t s) {
+  constexpr size_t smem = pw::r128::pass_b_smem();
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_b_r128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(pw::r128::pass_b_r128, pw::r128::NT, smem, 128 * 128, &grid);
+    if (e != cudaSuccess) return e;
+  }
+  pw::r128::pass_b_r128<<<grid, pw::r128::NT, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
 template <int N, bool HERM>
 cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
   constexpr size_t smem = pw::pass_b_smem<N>();
@@ -147,24 +187,33 @@ cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
 // ev: nullptr or three events recorded before pass A, between the passes and after pass B.
 template <int N>
 cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
-                          const pw::PassBArgs& b, cudaStream_t s, cudaEvent_t* ev) {
+                          const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-  e = array ? launch_a<N, true>(vmap, a, s) : launch_a<N, false>(vmap, a, s);
+  if constexpr (N == 128) {
+    if (x.mask) e = array ? launch_a_r128<true, true>(vmap, a, x, s) : launch_a_r128<false, true>(vmap, a, x, s);
+    else e = array ? launch_a_r128<true, false>(vmap, a, x, s) : launch_a_r128<false, false>(vmap, a, x, s);
+  } else {
+    e = array ? launch_a<N, true>(vmap, a, s) : launch_a<N, false>(vmap, a, s);
+  }
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
-  e = herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+  if constexpr (N == 128) {
+    e = herm ? launch_b_r128(b, s) : launch_b<N, false>(b, s);
+  } else {
+    e = herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+  }
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 cudaError_t dispatch(int N, bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
-                     const pw::PassBArgs& b, cudaStream_t s, cudaEvent_t* ev) {
+                     const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   switch (N) {
 #define PW_CASE(NN) \
   case NN:          \
-    return launch_passes<NN>(array, herm, vmap, a, b, s, ev);
+    return launch_passes<NN>(array, herm, vmap, a, b, x, s, ev);
     PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
     PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128)
 #undef PW_CASE
@@ -191,7 +240,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 // (2g floats of one d' run, b, a, d'/g, c'); box = one whole slice {2g, 1, 1, N/g, N}.
 pw_status make_vmap(pw_csd* h) {
   const int N = h->N;
-  const int g = N % 4 == 0 ? 4 : 2;
+  const int g = pw::vgroup_of(N);
   auto enc = encode_tiled();
   if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
@@ -236,6 +285,7 @@ pw_status build_tables(pw_csd* h, double z, bool farfield) {
   t.M0 = h->M0;
   t.tw = h->tw;
   t.Eout = h->Eout;
+  t.Ein = h->Ein;
   const int NN = N * N;
   const int threads = 256;
   const int blocks = (NN + threads - 1) / threads;
@@ -271,7 +321,17 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
   cudaEvent_t* ev = nullptr;
   if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
-  cudaError_t e = dispatch(h->N, array, herm, h->vmap, a, b, h->stream, ev);
+  R128Extra x{};
+  x.Ein = h->Ein;
+  x.mask = reinterpret_cast<const float2*>(h->mask);
+  x.ap_ithr = -1;
+  x.err = h->err;
+  if (h->aperture > 0.0) {
+    const double rp = h->aperture / h->d;
+    const double thr = rp * rp;  // the FP64 threshold of the table kernel; r^2 is an integer
+    x.ap_ithr = thr >= 2147483647.0 ? 2147483647 : (int)std::floor(thr);
+  }
+  cudaError_t e = dispatch(h->N, array, herm, h->vmap, a, b, x, h->stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
   // The output plane becomes the current plane; its CSDA is in W, its masks are unset.
   h->d = lz / (h->N * h->d);
@@ -382,6 +442,16 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
   h->tw = reinterpret_cast<float2*>(p);
   p += N * sizeof(float2);
   h->Eout = reinterpret_cast<float2*>(p);
+  p += N * sizeof(float2);
+  h->Ein = reinterpret_cast<float2*>(p);
+  p += N * sizeof(float2);
+  h->err = reinterpret_cast<int*>(p);
+  e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+  if (e != cudaSuccess) {
+    cudaFree(h->tables);
+    delete h;
+    return cuda_fail(e, "clearing the error flag");
+  }
   pw_status st = make_vmap(h);
   if (st != PW_OK) {
     cudaFree(h->tables);
@@ -428,6 +498,22 @@ pw_status pw_csd_reset(pw_csd* h, double dxi_m) {
   h->aperture = 0.0;
   h->lens_f = 0.0;
   h->mask = nullptr;
+  return PW_OK;
+}
+
+pw_status pw_csd_check(pw_csd* h) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the error flag");
+  if (flag) {
+    e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the error flag");
+    return fail(PW_ETIMEOUT, "a bounded device-side wait gave up; the last result is invalid");
+  }
   return PW_OK;
 }
 

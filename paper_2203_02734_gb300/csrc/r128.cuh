@@ -1,0 +1,431 @@
+// r128.cuh -- register-resident 2D DFT of a 128 x 128 slice for the two passes at N = 128.
+//
+// The 2D transform runs as three 2D Stockham stages with radices (p, q) = (8, 4), (4, 8),
+// (4, 4) (p = first slice index, q = second), 512 threads, 32 points per thread per stage:
+//   stage 1: butterfly (jp < 16, jq < 32), inputs (jp + 16 rp, jq + 32 rq), no twiddles,
+//            outputs (8 jp + rp, 4 jq + rq);
+//   stage 2: butterfly (jp < 32, jq < 16), inputs (jp + 32 rp, jq + 16 rq), twiddles
+//            w32^(rp (jp mod 8)) w32^(rq (jq mod 4)), outputs (32 (jp/8) + jp mod 8 + 8 rp,
+//            32 (jq/4) + jq mod 4 + 4 rq);
+//   stage 3: butterfly (jp < 32, jq < 32), inputs (jp + 32 rp, jq + 32 rq), twiddles
+//            w128^(rp jp) w128^(rq jq), outputs in natural order at the input positions;
+// (w_L = exp(SIGN 2 pi i / L)).  Points move between stages through one shared buffer whose
+// q index is XOR-swizzled per exchange (sw1, sw2) so that every half-warp touches 16 distinct
+// 8-byte bank pairs on both the write and the read side.
+#pragma once
+#include "propagate.cuh"
+
+namespace pw {
+namespace r128 {
+
+constexpr int N = 128;
+constexpr int NT = 512;
+
+__device__ __forceinline__ int sw1(int q) { return q ^ ((q >> 4) & 3); }
+__device__ __forceinline__ int sw2(int q) { return q ^ (((q >> 5) & 3) << 2); }
+
+template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int m) {
+  float2 w = tw[m];
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+
+template <int RP, int RQ, int SIGN> __device__ __forceinline__ void dft2d(float2 (&v)[RP][RQ]) {
+#pragma unroll
+  for (int rq = 0; rq < RQ; ++rq) {
+    float2 c[RP];
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) c[rp] = v[rp][rq];
+    Dft<RP, SIGN>::run(c);
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) v[rp][rq] = c[rp];
+  }
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) Dft<RQ, SIGN>::run(v[rp]);
+}
+
+// v[rp][rq] *= tw[mp * rp] (rp >= 1) and tw[mq * rq] (rq >= 1)
+template <int RP, int RQ, int SIGN>
+__device__ __forceinline__ void twiddle2d(float2 (&v)[RP][RQ], const float2* tw, int mp, int mq) {
+#pragma unroll
+  for (int rp = 1; rp < RP; ++rp) {
+    const float2 w = twid<SIGN>(tw, mp * rp);
+#pragma unroll
+    for (int rq = 0; rq < RQ; ++rq) v[rp][rq] = cmul(v[rp][rq], w);
+  }
+#pragma unroll
+  for (int rq = 1; rq < RQ; ++rq) {
+    const float2 w = twid<SIGN>(tw, mq * rq);
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) v[rp][rq] = cmul(v[rp][rq], w);
+  }
+}
+
+// Stages 2 and 3 from stage-1 outputs v (already the thread's 8 x 4 block), through buf.
+// On return w3[i][rp][rq] holds the transform at (jp3 + 32 rp, lane + 32 rq), jp3 = warp + 16 i.
+// Contract: buf is free on entry (all threads passed a barrier after its last use).
+template <int SIGN>
+__device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][4], float2* buf,
+                                         const float2* tw) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int rp = 0; rp < 8; ++rp)
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq) buf[(8 * warp + rp) * N + sw1(4 * lane + rq)] = v[rp][rq];
+  __syncthreads();
+  const int jq2 = t & 15, jp2 = t >> 4;
+  float2 u[4][8];
+#pragma unroll
+  for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq) u[rp][rq] = buf[(jp2 + 32 * rp) * N + sw1(jq2 + 16 * rq)];
+  twiddle2d<4, 8, SIGN>(u, tw, 4 * (jp2 & 7), 4 * (jq2 & 3));
+  dft2d<4, 8, SIGN>(u);
+  __syncthreads();
+#pragma unroll
+  for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq)
+      buf[((jp2 >> 3) * 32 + (jp2 & 7) + 8 * rp) * N + sw2((jq2 >> 2) * 32 + (jq2 & 3) + 4 * rq)] = u[rp][rq];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int jp3 = warp + 16 * i;
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq) w3[i][rp][rq] = buf[(jp3 + 32 * rp) * N + sw2(lane + 32 * rq)];
+    twiddle2d<4, 4, SIGN>(w3[i], tw, jp3, lane);
+    dft2d<4, 4, SIGN>(w3[i]);
+  }
+}
+
+// Pass A at N = 128, persistent.  Per point-1 pair (a, b): build W1(c, d) = s_ab F(c, d) G(a,c)
+// G(b,d) (or W0 x factors) in registers, 2D DFT (sign -1) over (c, d), natural-order slice into
+// shared memory, one TMA tensor store into the V layout.  F(c, d) = Ein(c) Ein(d) Y(c, d) m(c, d)
+// from the per-axis factors, the aperture test and the optional mask.
+template <bool ARRAY, bool MASK>
+__global__ void __launch_bounds__(NT, 1)
+    pass_a_r128(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
+                const float2* __restrict__ mask, int ap_ithr) {
+  extern __shared__ __align__(1024) float2 smem[];
+  float2* buf = smem;
+  float2* tw = buf + N * N;
+  float2* ein = tw + N;
+  float* gA = reinterpret_cast<float*>(ein + N);
+  float* gB = gA + N;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int i = t; i < N; i += NT) {
+    tw[i] = p.tw[i];
+    ein[i] = Ein[i];
+  }
+  // aperture: integer r^2 <= ap_ithr = floor of the FP64 threshold (same decision, no FP64 work)
+  auto inside = [&](int i, int j) {
+    const int ni = i - N / 2, nj = j - N / 2;
+    return ap_ithr < 0 || ni * ni + nj * nj <= ap_ithr;
+  };
+  // The thread's 32 points (c, d) = (warp + 16 rp, lane + 32 rq) are the same in every slice:
+  // their aperture pattern is one 32-bit mask.
+  unsigned inmask = 0;
+#pragma unroll
+  for (int rp = 0; rp < 8; ++rp)
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq)
+      if (inside(warp + 16 * rp, lane + 32 * rq)) inmask |= 1u << (rp * 4 + rq);
+  for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
+    const int a = ab / N, b = ab - a * N;
+    if (!ARRAY) {
+      for (int i = t; i < N; i += NT) {
+        gA[i] = p.G[a * N + i];
+        gB[i] = p.G[b * N + i];
+      }
+    }
+    __syncthreads();
+    // s_ab = A conj(F(a, b)), F(i, j) = Ein(i) Ein(j) Y(i, j) m(i, j)
+    float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
+    if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
+    float2 s_ab = cconj(fab);
+    if (!ARRAY) s_ab = cscale(s_ab, p.A);
+    const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    float2 ed[4];  // Ein(d) G(b, d)
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq) {
+      const int d = lane + 32 * rq;
+      ed[rq] = ARRAY ? ein[d] : cscale(ein[d], gB[d]);
+    }
+    float2 v[8][4];
+#pragma unroll
+    for (int rp = 0; rp < 8; ++rp) {
+      const int c = warp + 16 * rp;
+      const float2 sc = ARRAY ? cmul(s_ab, ein[c]) : cmul(s_ab, cscale(ein[c], gA[c]));
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq) {
+        const int d = lane + 32 * rq;
+        float2 x = cmul(sc, ed[rq]);
+        if (MASK) x = cmul(x, __ldg(mask + c * N + d));
+        if (ARRAY) x = cmul(x, __ldg(W0 + c * N + d));
+        v[rp][rq] = (inmask >> (rp * 4 + rq)) & 1u ? x : make_float2(0.f, 0.f);
+      }
+    }
+    dft2d<8, 4, -1>(v);
+    if (t == 0) bulk_wait_read_all();  // the previous slice's TMA store has left buf
+    __syncthreads();
+    float2 w3[2][4][4];
+    stages_23<-1>(v, w3, buf, tw);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+        for (int rq = 0; rq < 4; ++rq) buf[(warp + 16 * i + 32 * rp) * N + lane + 32 * rq] = w3[i][rp][rq];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tma_store_5d(&vmap, buf, 0, b, a, 0, 0);
+      bulk_commit();
+    }
+  }
+  if (t == 0) bulk_wait_all();
+}
+
+constexpr size_t pass_a_smem() { return (size_t)N * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float); }
+
+}  // namespace r128
+}  // namespace pw
+
+namespace pw {
+namespace r128 {
+
+// ---- cluster, mbarrier and bulk-copy helpers (inline PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of mbarrier m; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity) {
+  for (long it = 0; it < (1L << 24); ++it)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes, unsigned long long* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(smem_dst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+__device__ __forceinline__ unsigned map_rank(const void* local, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// Stages 2 and 3 through a half-size buffer (64 rows x 128): each exchange runs in two rounds.
+// Round h moves the rows p with hsel(p) == h; hsel mixes a register bit and a thread bit of p on
+// both sides, so every thread writes half and reads half of its points in each round, and at most
+// 32 points per thread are live at any time.
+//   exchange 1: hsel = (p & 1) ^ ((p >> 5) & 1), local row p >> 1, column sw1(q)
+//   exchange 2: hsel = ((p >> 3) & 1) ^ ((p >> 5) & 1), local row (p & 7) | ((p >> 4) << 3), column sw2(q)
+// The register index of each half is chosen with selects (no dynamic register indexing).
+__device__ __forceinline__ float2 sel2(bool c, float2 a, float2 b) { return c ? a : b; }
+
+template <int SIGN>
+__device__ __forceinline__ void stages_23_half(float2 (&v)[8][4], float2 (&w3)[2][4][4], float2* xb,
+                                              const float2* tw) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int jq2 = t & 15, jp2 = t >> 4;
+  // ---- exchange 1 ----
+  const bool wb = (warp >> 2) & 1;  // round 0 writes rp = 2k + wb
+  float2 y[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq) {
+      xb[(4 * warp + k) * N + sw1(4 * lane + rq)] = sel2(wb, v[2 * k + 1][rq], v[2 * k][rq]);
+      y[k][rq] = sel2(wb, v[2 * k][rq], v[2 * k + 1][rq]);
+    }
+  __syncthreads();
+  const bool jb = jp2 & 1;  // round h reads rp = 2k + (h ^ jb)
+  float2 z0[2][8], z1[2][8];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq)
+      z0[k][rq] = xb[((jp2 >> 1) + 16 * (2 * k + (jb ? 1 : 0))) * N + sw1(jq2 + 16 * rq)];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 4; ++rq) xb[(4 * warp + k) * N + sw1(4 * lane + rq)] = y[k][rq];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq)
+      z1[k][rq] = xb[((jp2 >> 1) + 16 * (2 * k + (jb ? 0 : 1))) * N + sw1(jq2 + 16 * rq)];
+  __syncthreads();
+  float2 u[4][8];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq) {
+      u[2 * k][rq] = sel2(jb, z1[k][rq], z0[k][rq]);
+      u[2 * k + 1][rq] = sel2(jb, z0[k][rq], z1[k][rq]);
+    }
+  twiddle2d<4, 8, SIGN>(u, tw, 4 * (jp2 & 7), 4 * (jq2 & 3));
+  dft2d<4, 8, SIGN>(u);
+  // ---- exchange 2 ----
+  const bool ub = (jp2 >> 3) & 1;  // round 0 writes rp = 2k + ub
+  float2 y2[2][8];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq) {
+      xb[((jp2 & 7) | (((jp2 >> 3) * 2 + k) << 3)) * N + sw2((jq2 >> 2) * 32 + (jq2 & 3) + 4 * rq)] =
+          sel2(ub, u[2 * k + 1][rq], u[2 * k][rq]);
+      y2[k][rq] = sel2(ub, u[2 * k][rq], u[2 * k + 1][rq]);
+    }
+  __syncthreads();
+  const bool cb = (warp >> 3) & 1;  // round h reads rp = 2k + (h ^ cb)
+  float2 q0[2][2][4], q1[2][2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq)
+        q0[i][k][rq] = xb[((warp & 7) | ((i + 2 * (2 * k + (cb ? 1 : 0))) << 3)) * N + sw2(lane + 32 * rq)];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq)
+      xb[((jp2 & 7) | (((jp2 >> 3) * 2 + k) << 3)) * N + sw2((jq2 >> 2) * 32 + (jq2 & 3) + 4 * rq)] = y2[k][rq];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq)
+        q1[i][k][rq] = xb[((warp & 7) | ((i + 2 * (2 * k + (cb ? 0 : 1))) << 3)) * N + sw2(lane + 32 * rq)];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq) {
+        w3[i][2 * k][rq] = sel2(cb, q1[i][k][rq], q0[i][k][rq]);
+        w3[i][2 * k + 1][rq] = sel2(cb, q0[i][k][rq], q1[i][k][rq]);
+      }
+    twiddle2d<4, 4, SIGN>(w3[i], tw, warp + 16 * i, lane);
+    dft2d<4, 4, SIGN>(w3[i]);
+  }
+}
+
+constexpr size_t kStageBytes = (size_t)N * N * sizeof(float2);  // prefetched stage-1 inputs
+constexpr size_t kXBytes = (size_t)N * N * sizeof(float2) / 2;     // half-size exchange buffer
+constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(float2); }
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Pass B at N = 128, persistent.  CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x +
+// k gridDim.x.  Every thread gathers exactly the 32 points (a, b) = (warp + 16 rp, lane + 32 rq)
+// of the strided column V(., ., c', d') that its stage-1 butterfly needs, one slice ahead, with
+// 8-byte asynchronous copies into a staging tile it alone reads: the gather of slice k+1 is in
+// flight while slice k is transformed, and no barrier guards the tile.  The inverse-sign 2D DFT
+// runs in registers (stages_23_half through a 64 KB exchange buffer), and the epilogue (scale,
+// output propagators, S on the diagonal) writes the conjugated column as the contiguous row
+// W(c', d', ., .) straight from registers (Hermitian store).
+__global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
+  extern __shared__ __align__(1024) float2 smem[];
+  float2* stg = smem;
+  float2* xb = stg + N * N;
+  float2* tw = xb + N * N / 2;
+  float2* eo = tw + N;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int g = vgroup<N>();
+  for (int i = t; i < N; i += NT) {
+    tw[i] = p.tw[i];
+    eo[i] = p.Eout[i];
+  }
+  auto gather = [&](int cdn) {
+    const float2* Vg = p.V + v_offset<N>(0, cdn / N, cdn % N);
+#pragma unroll
+    for (int rp = 0; rp < 8; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq) {
+        const int a = warp + 16 * rp, b = lane + 32 * rq;
+        cp_async8(stg + a * N + b, Vg + (size_t)(a * N + b) * g);
+      }
+  };
+  if (blockIdx.x < N * N) gather(blockIdx.x);
+  cp_async_commit();
+  __syncthreads();  // tw, eo
+  for (int cd = blockIdx.x; cd < N * N; cd += gridDim.x) {
+    const int c = cd / N, d = cd - c * N;
+    cp_async_wait_all();
+    float2 v[8][4];
+#pragma unroll
+    for (int rp = 0; rp < 8; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 4; ++rq) v[rp][rq] = stg[(warp + 16 * rp) * N + lane + 32 * rq];
+    dft2d<8, 4, +1>(v);  // consumes every staged value before the tile is refilled
+    if (cd + (int)gridDim.x < N * N) gather(cd + gridDim.x);
+    cp_async_commit();
+    float2 w3[2][4][4];
+    stages_23_half<+1>(v, w3, xb, tw);
+    const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
+    float2* Wrow = p.W + (size_t)cd * N * N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp) {
+        const int a = warp + 16 * i + 32 * rp;
+        const float2 ea = cmul(cconj(eo[a]), ecd);
+#pragma unroll
+        for (int rq = 0; rq < 4; ++rq) {
+          const int b = lane + 32 * rq;
+          const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
+          if (a == c && b == d) p.S[cd] = w.x;
+          Wrow[a * N + b] = cconj(w);
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+}  // namespace r128
+}  // namespace pw
