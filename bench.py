@@ -35,7 +35,10 @@ sys.path.insert(0, ROOT)
 
 import workloads as WL  # noqa: E402
 
-CFG = WL.GSM_APERTURE_LENS_N128
+WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
+             WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256}
+DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
+CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
 UNIT = "points/s"
 SAMPLE_N = 64  # grid of the bounded CPU sample of the same configuration
@@ -47,7 +50,24 @@ def parse_args():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    return p.parse_args()
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
+                   help="default: the N = 128 workload the metric is quoted on")
+    a = p.parse_args()
+    global CFG
+    CFG = WORKLOADS[a.workload]
+    return a
+
+
+def source_mask_host(N):
+    """Host-side (complex64) mask input of the workload: the aperture as a user mask for the N = 128
+    workload, the seeded phase screen for the N = 256 one."""
+    import numpy as np
+    if "corr_px" in CFG:
+        return WL.to_c64(WL.phase_screen(N, seed=WL.SEED, corr_px=CFG["corr_px"]))
+    n = np.arange(N)
+    r2 = (n[:, None] - N // 2) ** 2 + (N // 2 - n[None, :]) ** 2
+    rp = CFG["aperture"] / CFG["dxi"]
+    return (r2 <= rp * rp).astype(np.complex64)
 
 
 def dist_env():
@@ -62,7 +82,10 @@ def oracle_sample_step(N=SAMPLE_N):
     """One FP64 oracle propagation of the workload's configuration on an N x N grid,
     including the source build, S and mu.  Returns the number of points propagated."""
     import oracle as O
-    m = O.circle_aperture(N, CFG["dxi"], CFG["aperture"]) * O.thin_lens(N, CFG["dxi"], CFG["lam"], CFG["lens_f"])
+    if "corr_px" in CFG:
+        m = WL.phase_screen(N, seed=WL.SEED, corr_px=CFG["corr_px"])
+    else:
+        m = O.circle_aperture(N, CFG["dxi"], CFG["aperture"]) * O.thin_lens(N, CFG["dxi"], CFG["lam"], CFG["lens_f"])
     W0 = O.apply_mask(O.gsm_source(N, CFG["dxi"], CFG["sigma_S"], CFG["sigma_mu"], CFG["A"]), m)
     W, _ = O.propagate_fft(W0, CFG["dxi"], CFG["lam"], CFG["z"])
     O.spectral_density(W)
@@ -223,11 +246,17 @@ def run_ours(args):
     h = c.h
     P1 = CFG["P1"]
 
+    screen = "corr_px" in CFG
+    mask_dev0 = torch.from_numpy(source_mask_host(N)).cuda() if screen else None
+
     def step():
         pw.pw_csd_reset(h, CFG["dxi"])
         pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
-        pw.pw_source_aperture(h, CFG["aperture"])
-        pw.pw_source_lens(h, CFG["lens_f"])
+        if screen:
+            pw.pw_source_mask(h, mask_dev0.data_ptr())
+        else:
+            pw.pw_source_aperture(h, CFG["aperture"])
+            pw.pw_source_lens(h, CFG["lens_f"])
         pw.pw_propagate_fresnel(h, CFG["z"])
         pw.pw_spectral_density(h, S.data_ptr())
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
@@ -261,11 +290,7 @@ def run_ours(args):
     # End to end through the public API with host buffers: each step copies the aperture,
     # given as a user mask in pinned host memory, to the device and reads S and mu back into
     # pinned host memory; the same configuration as above, so the result is identical.
-    import numpy as np
-    n = np.arange(N)
-    r2 = (n[:, None] - N // 2) ** 2 + (N // 2 - n[None, :]) ** 2
-    rp = CFG["aperture"] / CFG["dxi"]
-    mask_h = torch.from_numpy((r2 <= rp * rp).astype(np.complex64)).pin_memory()
+    mask_h = torch.from_numpy(source_mask_host(N)).pin_memory()
     mask_d = torch.empty_like(mask_h, device="cuda")
     S_h = torch.empty((N, N), dtype=torch.float32).pin_memory()
     mu_h = torch.empty((N, N), dtype=torch.complex64).pin_memory()
@@ -275,7 +300,8 @@ def run_ours(args):
         pw.pw_csd_reset(h, CFG["dxi"])
         pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
         pw.pw_source_mask(h, mask_d.data_ptr())
-        pw.pw_source_lens(h, CFG["lens_f"])
+        if not screen:
+            pw.pw_source_lens(h, CFG["lens_f"])
         pw.pw_propagate_fresnel(h, CFG["z"])
         pw.pw_spectral_density(h, S.data_ptr())
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
@@ -317,9 +343,11 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": CFG["name"], "N": N, "points_per_step": pts, "dxi_m": CFG["dxi"],
-                   "lambda_m": CFG["lam"], "z_m": CFG["z"], "aperture_m": CFG["aperture"],
-                   "lens_f_m": CFG["lens_f"], "P1": list(P1), "parallelism": "replicas x%d" % world,
-                   "l2": "inputs larger than L2: 2 x 2.1 GB CSDA buffers stream through HBM every step"},
+                   "lambda_m": CFG["lam"], "z_m": CFG["z"], "aperture_m": CFG.get("aperture"),
+                   "lens_f_m": CFG.get("lens_f"), "phase_screen_corr_px": CFG.get("corr_px"), "P1": list(P1),
+                   "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2: 2 x %.1f GB CSDA buffers stream through HBM every step"
+                         % (8 * pts / 1e9)},
         "roofline": {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern),
                      "algorithmic_bytes_per_launch": bytes_launch,

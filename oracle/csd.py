@@ -32,7 +32,8 @@ __all__ = [
     "axis_coords", "output_sampling", "q", "gsm_source", "circle_aperture", "thin_lens",
     "apply_mask", "centred_dft2", "propagate_fft", "propagate_direct", "propagate_rows",
     "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
-    "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters",
+    "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
+    "propagate_rows_gsm",
 ]
 
 
@@ -215,6 +216,53 @@ def propagate_rows(source_slice, N, dxi, lam, z, rows, farfield=False):
     out = centred_dft2(inner, axes=(1, 2), sign=-1)
     qout = q(z, _r2_grid(N, dx), lam)
     for r, (a, b) in enumerate(rows):
+        out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
+    return out
+
+
+def propagate_rows_blocks(source_block, N, dxi, lam, z, rows, farfield=False):
+    """Same rows as propagate_rows, with the point-1 sum taken one first index at a time:
+    source_block(i1) returns W0[i1, :, :, :] (N x N x N), and for each i1 the sum over j1 is a
+    matrix product of the (rows x N) exponential weights with that block.  For large N."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    rows = list(rows)
+    qin = np.ones((N, N), dtype=np.complex128) if farfield else q(z, _r2_grid(N, dxi), lam)
+    c = np.empty((len(rows), N, N), dtype=np.complex128)
+    for r, (a, b) in enumerate(rows):
+        ph = (X[a] * x[:, None] + Y[b] * y[None, :]) / (lam * z)
+        c[r] = np.conj(qin) * np.exp(2j * np.pi * ph)
+    inner = np.zeros((len(rows), N * N), dtype=np.complex128)
+    for i1 in range(N):
+        inner += c[:, i1, :] @ source_block(i1).reshape(N, N * N)
+    inner = inner.reshape(len(rows), N, N) * qin[None]
+    out = centred_dft2(inner, axes=(1, 2), sign=-1)
+    qout = q(z, _r2_grid(N, dx), lam)
+    for r, (a, b) in enumerate(rows):
+        out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
+    return out
+
+
+def propagate_rows_gsm(m, N, dxi, lam, z, sigma_S, sigma_mu, A, rows, farfield=False):
+    """Rows of the propagated CSDA of the masked GSM source W0 = A m*(xi1) g(i1,i2) g(j1,j2) m(xi2)
+    (g the per-axis GSM factor of Sec. 5.4, reading R1), with the point-1 sum of Eq. W_fresnel
+    written as sum_{i1} g(i1, i2) sum_{j1} w(i1, j1) m*(i1, j1) g(j1, j2), i.e. G^T (w o m*) G
+    for the exponential weights w of each row (the GSM factor is separable).  O(N^3) per row."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    m = np.asarray(m, dtype=np.complex128)
+    g = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * sigma_S ** 2)
+               - (x[:, None] - x[None, :]) ** 2 / (2 * sigma_mu ** 2))
+    qin = np.ones((N, N), dtype=np.complex128) if farfield else q(z, _r2_grid(N, dxi), lam)
+    qout = q(z, _r2_grid(N, dx), lam)
+    out = np.empty((len(rows), N, N), dtype=np.complex128)
+    for r, (a, b) in enumerate(rows):
+        ph = (X[a] * x[:, None] + Y[b] * y[None, :]) / (lam * z)
+        w = np.conj(qin) * np.exp(2j * np.pi * ph)
+        inner = A * m * (g.T @ (w * np.conj(m)) @ g) * qin
+        out[r] = centred_dft2(inner, axes=(0, 1), sign=-1)
         out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
     return out
 

@@ -13,6 +13,7 @@
 
 #include "../../include/pywolf_gb.h"
 #include "propagate.cuh"
+#include "d256.cuh"
 #include "r128.cuh"
 
 namespace {
@@ -82,7 +83,7 @@ namespace {
 bool supported(int N) {
   switch (N) {
     case 2: case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64:
-    case 96: case 128:
+    case 96: case 128: case 256:
       return true;
     default:
       return false;
@@ -169,6 +170,47 @@ cudaError_t launch_b_r128(const pw::PassBArgs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Persistent launch of a kernel compiled for clusters of `cs` CTAs: as many clusters as can be
+// co-resident (queried once per kernel).
+template <class K, class... Args>
+cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (*grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nclusters = 0;
+    cfg.gridDim = dim3(cs * num_sms());
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    *grid = nclusters * cs;
+  }
+  cfg.gridDim = dim3(*grid);
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <bool ARRAY, bool MASK>
+cudaError_t launch_a_d256(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
+  static int grid = 0;
+  return launch_clusters(pw::d256::pass_a_d256<ARRAY, MASK>, pw::d256::CS, pw::d256::NT, pw::d256::pass_a_smem(),
+                         &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr);
+}
+
+cudaError_t launch_b_d256(const pw::PassBArgs& b, cudaStream_t s) {
+  static int grid = 0;
+  return launch_clusters(pw::d256::pass_b_d256, pw::d256::CS, pw::d256::NT, pw::d256::pass_b_smem(), &grid, s, b);
+}
+
 template <int N, bool HERM>
 cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
   constexpr size_t smem = pw::pass_b_smem<N>();
@@ -193,6 +235,9 @@ cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const 
   if constexpr (N == 128) {
     if (x.mask) e = array ? launch_a_r128<true, true>(vmap, a, x, s) : launch_a_r128<false, true>(vmap, a, x, s);
     else e = array ? launch_a_r128<true, false>(vmap, a, x, s) : launch_a_r128<false, false>(vmap, a, x, s);
+  } else if constexpr (N == 256) {
+    if (x.mask) e = array ? launch_a_d256<true, true>(vmap, a, x, s) : launch_a_d256<false, true>(vmap, a, x, s);
+    else e = array ? launch_a_d256<true, false>(vmap, a, x, s) : launch_a_d256<false, false>(vmap, a, x, s);
   } else {
     e = array ? launch_a<N, true>(vmap, a, s) : launch_a<N, false>(vmap, a, s);
   }
@@ -200,6 +245,8 @@ cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const 
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if constexpr (N == 128) {
     e = herm ? launch_b_r128(b, s) : launch_b<N, false>(b, s);
+  } else if constexpr (N == 256) {
+    e = herm ? launch_b_d256(b, s) : cudaErrorNotSupported;
   } else {
     e = herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
   }
@@ -215,7 +262,7 @@ cudaError_t dispatch(int N, bool array, bool herm, const CUtensorMap& vmap, cons
   case NN:          \
     return launch_passes<NN>(array, herm, vmap, a, b, x, s, ev);
     PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
-    PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128)
+    PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128) PW_CASE(256)
 #undef PW_CASE
     default:
       return cudaErrorInvalidValue;
@@ -246,7 +293,9 @@ pw_status make_vmap(pw_csd* h) {
   const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
   cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
   cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
-  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(N / g), (cuuint32_t)N};
+  // N = 256: each CTA of a cluster stores a tile of N / 4 columns (d256.cuh)
+  const int cols = N == 256 ? N / pw::d256::CS : N;
+  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)N};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(&h->vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)h->work, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -301,6 +350,10 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
   if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
+  const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
+  if (h->N == 256 && !herm)
+    return fail(PW_EUNSUPPORTED, "N = 256 needs a Hermitian source (the general strided-store second pass "
+                                 "exists for N <= 128 only)");
   pw_status st = build_tables(h, z, farfield);
   if (st != PW_OK) return st;
   const bool array = h->kind != SRC_GSM;
@@ -318,7 +371,6 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   b.S = h->S;
   const double lz = h->lambda * z;
   b.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
-  const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
   cudaEvent_t* ev = nullptr;
   if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
   R128Extra x{};

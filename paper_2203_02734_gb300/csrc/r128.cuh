@@ -13,6 +13,7 @@
 // q index is XOR-swizzled per exchange (sw1, sw2) so that every half-warp touches 16 distinct
 // 8-byte bank pairs on both the write and the read side.
 #pragma once
+#include "cluster.cuh"
 #include "propagate.cuh"
 
 namespace pw {
@@ -197,55 +198,6 @@ constexpr size_t pass_a_smem() { return (size_t)N * N * sizeof(float2) + 2 * N *
 namespace pw {
 namespace r128 {
 
-// ---- cluster, mbarrier and bulk-copy helpers (inline PTX) ----
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(m)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for phase `parity` of mbarrier m; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, unsigned parity) {
-  for (long it = 0; it < (1L << 24); ++it)
-    if (mbar_try_wait(m, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes, unsigned long long* m) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(smem_dst)),
-               "l"(gsrc), "r"(bytes), "r"(smem_u32(m))
-               : "memory");
-}
-__device__ __forceinline__ unsigned map_rank(const void* local, unsigned rank) {
-  unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ float2 ld_cluster(unsigned addr) {
-  float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
-  return v;
-}
-
 // Stages 2 and 3 through a half-size buffer (64 rows x 128): each exchange runs in two rounds.
 // Round h moves the rows p with hsel(p) == h; hsel mixes a register bit and a thread bit of p on
 // both sides, so every thread writes half and reads half of its points in each round, and at most
@@ -353,12 +305,6 @@ __device__ __forceinline__ void stages_23_half(float2 (&v)[8][4], float2 (&w3)[2
 constexpr size_t kStageBytes = (size_t)N * N * sizeof(float2);  // prefetched stage-1 inputs
 constexpr size_t kXBytes = (size_t)N * N * sizeof(float2) / 2;     // half-size exchange buffer
 constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(float2); }
-
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Pass B at N = 128, persistent.  CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x +
 // k gridDim.x.  Every thread gathers exactly the 32 points (a, b) = (warp + 16 rp, lane + 32 rq)

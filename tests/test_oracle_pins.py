@@ -118,6 +118,29 @@ def test_propagate_rows_equals_fft_route():
     assert rel(gotf[1], fullf[3, 11]) < 1e-12
 
 
+def test_propagate_rows_blocks_equals_fft_route():
+    N = 12
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM), _rand_mask(N, 6))
+    rows = [(6, 6), (1, 10)]
+    for ff in (False, True):
+        full, _ = O.propagate_fft(W0, DXI, LAM, 0.4, ff)
+        got = O.propagate_rows_blocks(lambda i: W0[i], N, DXI, LAM, 0.4, rows, ff)
+        for r, (a, b) in enumerate(rows):
+            assert rel(got[r], full[a, b]) < 1e-12
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_propagate_rows_gsm_equals_fft_route(farfield):
+    N = 14
+    m = _rand_mask(N, 8)
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM, 1.4), m)
+    full, _ = O.propagate_fft(W0, DXI, LAM, 0.45, farfield)
+    rows = [(7, 7), (2, 11), (13, 0)]
+    got = O.propagate_rows_gsm(m, N, DXI, LAM, 0.45, SS, SM, 1.4, rows, farfield)
+    for r, (a, b) in enumerate(rows):
+        assert rel(got[r], full[a, b]) < 1e-12
+
+
 # --------------------------------------------------------------------------- invariants
 @pytest.mark.parametrize("farfield", [False, True])
 def test_parseval_and_trace(farfield):
