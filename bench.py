@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 import workloads as WL  # noqa: E402
 
 WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
-             WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256}
+             WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256,
+             WL.POLYCHROMATIC_BATCH["name"]: WL.POLYCHROMATIC_BATCH}
 DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
 CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
@@ -366,9 +367,111 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_instances():
+    """The polychromatic workload: 16 frequencies of a Gaussian spectrum (weights as GSM
+    amplitudes) x N in {64, 96, 128} x z in {0.1, 0.5, 1, 5} m = 192 instances."""
+    lams, wts = WL.polychromatic_samples(CFG["lam0"], CFG["fwhm_lam"], CFG["n_freq"])
+    out = []
+    for lam, wt in zip(lams, wts):
+        for N in CFG["Ns"]:
+            for z in CFG["zs"]:
+                out.append(dict(N=N, lam=float(lam), A=float(wt), z=z))
+    return out
+
+
+def run_batch(args):
+    """Batched polychromatic run: all instances in one persistent launch, captured once in a CUDA
+    graph and replayed; S and mu of every instance.  Reported next to the plain path (the
+    single-instance calls, one instance after the other) on the same GPU."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+
+    torch.cuda.set_device(0)
+    specs = batch_instances()
+    s = torch.cuda.Stream()
+    bufs, insts = [], []
+    for sp in specs:
+        N = sp["N"]
+        S = torch.empty((N, N), dtype=torch.float32, device="cuda")
+        mu = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+        bufs.append((S, mu))
+        insts.append(pw.pw_instance(N, CFG["dxi"], sp["lam"], sp["z"], 0, CFG["sigma_S"], CFG["sigma_mu"], sp["A"],
+                                    0.0, 0.0, None, N // 2, N // 2, None, S.data_ptr(), mu.data_ptr()))
+    pool = 4
+    nb = pw.pw_batch_workspace_bytes(insts, pool)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(insts, pool, ws.data_ptr(), nb, s.cuda_stream)
+    chunk = pw.pw_batch_autotune(b)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pw.pw_batch_run(b)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clock = ClockSampler(torch.cuda.current_device())
+    t0 = time.time()
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    clocks = clock.stop(t0, t1)
+    pw.pw_batch_check(b)
+    ms = e0.elapsed_time(e1) / args.steps
+    pts = sum(sp["N"] ** 4 for sp in specs)
+    # plain path: the same instances through the single-instance calls, one after the other
+    maxN = max(sp["N"] for sp in specs)
+    W = torch.empty(maxN ** 4, dtype=torch.complex64, device="cuda")
+    work = torch.empty(maxN ** 4, dtype=torch.complex64, device="cuda")
+    # one handle per (N, wavelength): create them up front (not timed)
+    hl = {}
+    for sp in specs:
+        key = (sp["N"], sp["lam"])
+        if key not in hl:
+            hl[key] = pw.pw_csd_create(sp["N"], CFG["dxi"], sp["lam"], W.data_ptr(), W.numel() * 8, work.data_ptr(),
+                                       work.numel() * 8, torch.cuda.current_stream().cuda_stream)
+
+    def plain_exact():
+        for sp, (S, mu) in zip(specs, bufs):
+            h = hl[(sp["N"], sp["lam"])]
+            pw.pw_csd_reset(h, CFG["dxi"])
+            pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], sp["A"])
+            pw.pw_propagate_fresnel(h, sp["z"])
+            pw.pw_spectral_density(h, S.data_ptr())
+            pw.pw_degree_of_coherence(h, sp["N"] // 2, sp["N"] // 2, mu.data_ptr())
+
+    plain_exact()
+    torch.cuda.synchronize()
+    e0.record()
+    reps = max(1, min(args.steps, 5))
+    for _ in range(reps):
+        plain_exact()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / reps
+    for h in hl.values():
+        pw.pw_csd_destroy(h)
+    pw.pw_batch_destroy(b)
+    line = {"metric": METRIC, "value": pts / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CFG["name"], "instances": len(specs), "points_per_step": pts,
+                       "Ns": list(CFG["Ns"]), "zs": list(CFG["zs"]), "n_freq": CFG["n_freq"],
+                       "outputs": "S and mu per instance", "pool": pool, "chunk": chunk,
+                       "launch": "one persistent launch per step, replayed from a CUDA graph"},
+            "plain_path": {"value": pts / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
+                           "what": "the same instances through the single-instance calls, one after another"},
+            "gpu_launches": 4 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
+    elif CFG is WL.POLYCHROMATIC_BATCH:
+        run_batch(a)
     else:
         run_ours(a)

@@ -160,6 +160,67 @@ pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
 pw_status pw_csd_enable_timing(pw_csd* h, int max_props);
 pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count);
 
+/* ---- Batched runs: many instances in one persistent launch --------------------------------
+ * For the polychromatic case of Sec. 6 (future work in the paper: many frequencies of a
+ * spectrum), several distances and uneven grid sizes.  Each instance is one propagation of a
+ * GSM source (Sec. 5.4) times an optional aperture, thin lens and mask from its source plane;
+ * it yields S (Eq. defS) and mu(P1, .) (Eq. defMu) of its output plane, and the whole propagated
+ * CSDA when dev_W is given.  All instances run in one persistent launch that walks a work list
+ * of (instance, pass, slice chunk) items: pass-B work of an instance starts after its pass-A work,
+ * and the half-transformed CSDAs share a pool of `pool` buffers of the largest N (instance i uses
+ * slot i mod pool).  pw_batch_run enqueues only device work (no allocation, no synchronisation),
+ * so the caller may capture it in a CUDA graph and replay it. */
+typedef struct pw_instance {
+  int N;                 /* grid size: 16, 32, 64, 96 or 128 */
+  double dxi_m, lambda_m, z_m;
+  int farfield;          /* 0: Fresnel (Eq. W_fresnel), 1: far field (Eq. W_farfield) */
+  double sigma_S_m, sigma_mu_m, amplitude;  /* GSM source; amplitude may carry a spectral weight */
+  double aperture_m;     /* <= 0: none */
+  double lens_f_m;       /* 0: none */
+  const pw_c32* dev_mask;/* N x N device mask or NULL */
+  int iP, jP;            /* P1 of mu */
+  pw_c32* dev_W;         /* N^4 device output or NULL (S and mu only) */
+  float* dev_S;          /* N x N device output (required) */
+  pw_c32* dev_mu;        /* N x N device output or NULL */
+} pw_instance;
+
+typedef struct pw_batch pw_batch; /* opaque */
+
+/* Bytes of device workspace pw_batch_create needs for these instances and this pool depth
+ * (tables, work list, counters and `pool` half-transformed buffers of the largest N). */
+size_t pw_batch_workspace_bytes(const pw_instance* inst, int n, int pool);
+
+/* Validate the instances (N in {16, 32, 64, 96, 128}, finite positive lengths, P1 inside the
+ * grid, dev_S given), lay out the caller-owned workspace (>= pw_batch_workspace_bytes) and upload
+ * the descriptors and the work list (synchronises `stream`).  The output pointers are kept. */
+pw_status pw_batch_create(pw_batch** out, const pw_instance* inst, int n, int pool, void* dev_workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Enqueue one batched run on the batch's stream: counter reset, FP64 tables of every instance,
+ * the persistent launch, mu.  Asynchronous; no allocation; capturable in a CUDA graph. */
+pw_status pw_batch_run(pw_batch* b);
+
+/* Synchronise and report PW_ETIMEOUT if a bounded dependency wait of a run gave up since the
+ * last check (the affected outputs are invalid); clears the condition. */
+pw_status pw_batch_check(pw_batch* b);
+
+/* Slices per work item (>= 4; default 8).  Rebuilds the work list (synchronises). */
+pw_status pw_batch_set_chunk(pw_batch* b, int chunk);
+pw_status pw_batch_get_chunk(const pw_batch* b, int* chunk);
+
+/* Time the run for each candidate chunk size (4 ... 64) and keep the fastest; returns it in
+ * *chunk_out if non-NULL.  Runs the batch several times (synchronises). */
+pw_status pw_batch_autotune(pw_batch* b, int* chunk_out);
+
+/* Failure-detection test hook (no counterpart in the paper): leave the pass-A work of
+ * `instance` out of the work list and bound every dependency wait to wait_s seconds, so that
+ * the pass-B work of that instance gives up waiting and the next pw_batch_check returns
+ * PW_ETIMEOUT while the other instances complete.  No device fault is involved. */
+pw_status pw_batch_inject_stall(pw_batch* b, int instance, double wait_s);
+
+/* Synchronise the stream and free the host-side state (the workspace belongs to the caller). */
+pw_status pw_batch_destroy(pw_batch* b);
+
 /* Allocation-free Fresnel propagation of a GSM source (the paper has no counterpart).
  * For callers that cannot allocate device memory: applications whose framework reserves all
  * device memory in its own pool and does not let libraries call the CUDA allocator, and

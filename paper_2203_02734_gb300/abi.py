@@ -53,6 +53,32 @@ for _name, (_res, _args) in SIGNATURES.items():
     _f.argtypes = _args
 
 
+class pw_instance(ctypes.Structure):
+    """Mirror of the C struct pw_instance (include/pywolf_gb.h)."""
+    _fields_ = [("N", _i), ("dxi_m", _d), ("lambda_m", _d), ("z_m", _d), ("farfield", _i),
+                ("sigma_S_m", _d), ("sigma_mu_m", _d), ("amplitude", _d), ("aperture_m", _d),
+                ("lens_f_m", _d), ("dev_mask", _vp), ("iP", _i), ("jP", _i), ("dev_W", _vp),
+                ("dev_S", _vp), ("dev_mu", _vp)]
+
+
+_IP = ctypes.POINTER(pw_instance)
+for _name, (_res, _args) in {
+    "pw_batch_workspace_bytes": (ctypes.c_size_t, [_IP, _i, _i]),
+    "pw_batch_create": (_i, [ctypes.POINTER(_vp), _IP, _i, _i, _vp, ctypes.c_size_t, _vp]),
+    "pw_batch_run": (_i, [_vp]),
+    "pw_batch_check": (_i, [_vp]),
+    "pw_batch_set_chunk": (_i, [_vp, _i]),
+    "pw_batch_get_chunk": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pw_batch_autotune": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pw_batch_inject_stall": (_i, [_vp, _i, _d]),
+    "pw_batch_destroy": (_i, [_vp]),
+}.items():
+    SIGNATURES[_name] = (_res, _args)
+    _f = getattr(LIB, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
 class PwError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (LIB.pw_status_string(status).decode(), msg))
@@ -158,3 +184,52 @@ def pw_propagate_gsm_fresnel_noalloc(N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_m
     _check(LIB.pw_propagate_gsm_fresnel_noalloc(N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_mu_m, amplitude,
                                                  aperture_m, lens_f_m, dev_mask, dev_W_out, W_bytes, dev_S_out,
                                                  stream))
+
+
+def _instances(insts):
+    arr = (pw_instance * len(insts))(*insts)
+    return arr
+
+
+def pw_batch_workspace_bytes(insts, pool):
+    arr = _instances(insts)
+    return int(LIB.pw_batch_workspace_bytes(arr, len(insts), pool))
+
+
+def pw_batch_create(insts, pool, dev_ws, ws_bytes, stream=0):
+    arr = _instances(insts)
+    b = _vp()
+    _check(LIB.pw_batch_create(ctypes.byref(b), arr, len(insts), pool, dev_ws, ws_bytes, stream))
+    return b.value
+
+
+def pw_batch_run(b):
+    _check(LIB.pw_batch_run(b))
+
+
+def pw_batch_check(b):
+    _check(LIB.pw_batch_check(b))
+
+
+def pw_batch_set_chunk(b, chunk):
+    _check(LIB.pw_batch_set_chunk(b, chunk))
+
+
+def pw_batch_get_chunk(b):
+    c = _i()
+    _check(LIB.pw_batch_get_chunk(b, ctypes.byref(c)))
+    return c.value
+
+
+def pw_batch_autotune(b):
+    c = _i()
+    _check(LIB.pw_batch_autotune(b, ctypes.byref(c)))
+    return c.value
+
+
+def pw_batch_inject_stall(b, instance, wait_s):
+    _check(LIB.pw_batch_inject_stall(b, instance, wait_s))
+
+
+def pw_batch_destroy(b):
+    _check(LIB.pw_batch_destroy(b))

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpywolf_gb.so")
 SRC = os.path.join(HERE, "csrc", "pywolf_gb.cu")
-SRCS = [SRC, os.path.join(HERE, "csrc", "noalloc.cu")]
+SRCS = [SRC, os.path.join(HERE, "csrc", "noalloc.cu"), os.path.join(HERE, "csrc", "batch.cu")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

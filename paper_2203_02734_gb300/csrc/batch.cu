@@ -1,0 +1,361 @@
+// batch.cu -- C ABI of the batched run (pw_batch_*): instance descriptors, workspace layout,
+// item list, launch sequence (counter reset, FP64 tables, one persistent launch, mu) and the
+// chunk-size autotuner.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/pywolf_gb.h"
+#include "batch.cuh"
+
+namespace pwi {
+void set_last_error(const char* msg);  // pywolf_gb.cu
+}
+
+namespace {
+
+pw_status fail(pw_status s, const char* fmt, ...) {
+  char msg[320];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  pwi::set_last_error(msg);
+  return s;
+}
+
+pw_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(PW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+bool batch_n(int N) { return N == 16 || N == 32 || N == 64 || N == 96 || N == 128; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout (offsets from the base, each part 256-byte aligned).
+struct Layout {
+  size_t inst, targs, mu, items, counters, tables, pool, total;
+  int max_items;
+  size_t slot_bytes;
+};
+
+constexpr int kMinChunk = 4;
+
+Layout layout(const pw_instance* in, int n, int pool) {
+  Layout L{};
+  size_t off = 0;
+  L.inst = off;
+  off = align256(off + sizeof(pw::batch::Inst) * n);
+  L.targs = off;
+  off = align256(off + sizeof(pw::TableArgs) * n);
+  L.mu = off;
+  off = align256(off + sizeof(float2*) * n);
+  long items = 0;
+  int maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    const long s = (long)in[i].N * in[i].N;
+    items += 2 * ((s + kMinChunk - 1) / kMinChunk);
+    if (in[i].N > maxN) maxN = in[i].N;
+  }
+  L.max_items = (int)items;
+  L.items = off;
+  off = align256(off + sizeof(pw::batch::Item) * items);
+  L.counters = off;
+  off = align256(off + sizeof(int) * (2 * (size_t)n + 2));
+  L.tables = off;
+  for (int i = 0; i < n; ++i) {
+    const size_t N = in[i].N, NN = N * N;
+    off = align256(off + NN * sizeof(float2));  // F
+    off = align256(off + NN * sizeof(float));   // G
+    off = align256(off + N * sizeof(float2));   // twiddles
+    off = align256(off + N * sizeof(float2));   // output propagators
+    off = align256(off + NN * sizeof(float2));  // W(P1, .)
+  }
+  L.pool = off;
+  L.slot_bytes = align256((size_t)maxN * maxN * maxN * maxN * sizeof(float2));
+  off += L.slot_bytes * pool;
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct pw_batch {
+  int n, pool, chunk;
+  char* base;
+  Layout L;
+  cudaStream_t stream;
+  std::vector<pw::batch::Inst> inst;
+  std::vector<int> stalled;  // instances whose pass-A items are left out (failure-detection test)
+  int nitems;
+  long long wait_cycles;
+};
+
+namespace {
+
+pw_status build_items(pw_batch* b) {
+  std::vector<pw::batch::Item> items;
+  auto add = [&](int i, int pass) {
+    if (pass == 0 && b->stalled[i]) return;
+    const int s = b->inst[i].slices;
+    for (int s0 = 0; s0 < s; s0 += b->chunk) items.push_back({i, pass, s0, s0 + b->chunk < s ? s0 + b->chunk : s});
+  };
+  // one-instance lookahead: A(0), A(1), B(0), A(2), B(1), ..., B(n-1)
+  add(0, 0);
+  for (int i = 1; i < b->n; ++i) {
+    add(i, 0);
+    add(i - 1, 1);
+  }
+  add(b->n - 1, 1);
+  if ((int)items.size() > b->L.max_items) return fail(PW_EINVAL, "item list exceeds the workspace");
+  b->nitems = (int)items.size();
+  cudaError_t e = cudaMemcpyAsync(b->base + b->L.items, items.data(), items.size() * sizeof(pw::batch::Item),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the item list");
+  return PW_OK;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pw_batch_workspace_bytes(const pw_instance* inst, int n, int pool) {
+  if (!inst || n <= 0 || pool <= 0) return 0;
+  return layout(inst, n, pool).total;
+}
+
+pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool, void* dev_ws, size_t ws_bytes,
+                          void* stream) {
+  pwi::set_last_error("");
+  if (!out) return fail(PW_EINVAL, "out is null");
+  *out = nullptr;
+  if (!in || n <= 0) return fail(PW_EINVAL, "need at least one instance");
+  if (pool <= 0) return fail(PW_EINVAL, "pool depth must be >= 1");
+  if (!dev_ws) return fail(PW_EINVAL, "workspace is null");
+  for (int i = 0; i < n; ++i) {
+    const pw_instance& q = in[i];
+    if (!batch_n(q.N)) return fail(PW_EUNSUPPORTED, "instance %d: N = %d (batched runs take N in {16, 32, 64, 96, 128})", i, q.N);
+    if (!finite_pos(q.dxi_m) || !finite_pos(q.lambda_m) || !finite_pos(q.z_m) || !finite_pos(q.sigma_S_m) ||
+        !finite_pos(q.sigma_mu_m))
+      return fail(PW_EINVAL, "instance %d: lengths must be finite and > 0", i);
+    if (!std::isfinite(q.amplitude) || !std::isfinite(q.aperture_m) || !std::isfinite(q.lens_f_m))
+      return fail(PW_EINVAL, "instance %d: amplitude, aperture and focal length must be finite", i);
+    if (q.iP < 0 || q.jP < 0 || q.iP >= q.N || q.jP >= q.N) return fail(PW_EINVAL, "instance %d: P1 outside the grid", i);
+    if (!q.dev_S) return fail(PW_EINVAL, "instance %d: dev_S is required", i);
+  }
+  const Layout L = layout(in, n, pool);
+  if (ws_bytes < L.total) return fail(PW_ESIZE, "workspace needs %zu bytes (got %zu)", L.total, ws_bytes);
+  pw_batch* b = new pw_batch{};
+  b->n = n;
+  b->pool = pool;
+  b->chunk = 8;
+  b->base = reinterpret_cast<char*>(dev_ws);
+  b->L = L;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->stalled.assign(n, 0);
+  b->wait_cycles = 2000000000LL;  // ~1 s at 2 GHz
+  std::vector<pw::TableArgs> targs(n);
+  std::vector<float2*> mus(n);
+  b->inst.resize(n);
+  size_t off = L.tables;
+  for (int i = 0; i < n; ++i) {
+    const pw_instance& q = in[i];
+    const int N = q.N;
+    const size_t NN = (size_t)N * N;
+    pw::batch::Inst& d = b->inst[i];
+    d.N = N;
+    d.iP = q.iP;
+    d.jP = q.jP;
+    d.slices = (int)NN;
+    d.A = (float)q.amplitude;
+    const double lz = q.lambda_m * q.z_m;
+    d.scale = (float)((q.dxi_m * q.dxi_m / lz) * (q.dxi_m * q.dxi_m / lz));
+    float2* F = reinterpret_cast<float2*>(b->base + off);
+    off = align256(off + NN * sizeof(float2));
+    float* G = reinterpret_cast<float*>(b->base + off);
+    off = align256(off + NN * sizeof(float));
+    float2* tw = reinterpret_cast<float2*>(b->base + off);
+    off = align256(off + N * sizeof(float2));
+    float2* Eo = reinterpret_cast<float2*>(b->base + off);
+    off = align256(off + N * sizeof(float2));
+    d.row = reinterpret_cast<float2*>(b->base + off);
+    off = align256(off + NN * sizeof(float2));
+    d.F = F;
+    d.G = G;
+    d.tw = tw;
+    d.Eout = Eo;
+    d.V = reinterpret_cast<float2*>(b->base + L.pool + L.slot_bytes * (i % pool));
+    d.W = reinterpret_cast<float2*>(q.dev_W);
+    d.S = q.dev_S;
+    mus[i] = reinterpret_cast<float2*>(q.dev_mu);
+    // FP64 tables: same quantities as the single-instance path (propagator phases in turns)
+    pw::TableArgs& t = targs[i];
+    t = pw::TableArgs{};
+    t.N = N;
+    const double invf = q.lens_f_m != 0.0 ? 1.0 / q.lens_f_m : 0.0;
+    const double base = q.dxi_m * q.dxi_m / (2.0 * q.lambda_m);
+    t.Kin = q.farfield ? -base * invf : base * (1.0 / q.z_m - invf);
+    const double dx = lz / (N * q.dxi_m);
+    t.Kout = dx * dx / (2.0 * lz);
+    t.gs = q.dxi_m * q.dxi_m / (4.0 * q.sigma_S_m * q.sigma_S_m);
+    t.gm = q.dxi_m * q.dxi_m / (2.0 * q.sigma_mu_m * q.sigma_mu_m);
+    if (q.aperture_m > 0.0) {
+      const double rp = q.aperture_m / q.dxi_m;
+      t.ap_thr = rp * rp;
+    } else {
+      t.ap_thr = -1.0;
+    }
+    t.mask = reinterpret_cast<const float2*>(q.dev_mask);
+    t.F = F;
+    t.G = G;
+    t.tw = tw;
+    t.Eout = Eo;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->base + L.inst, b->inst.data(), sizeof(pw::batch::Inst) * n,
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->base + L.targs, targs.data(), sizeof(pw::TableArgs) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->base + L.mu, mus.data(), sizeof(float2*) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pw::batch::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)pw::batch::smem_bytes());
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch set-up");
+  }
+  pw_status st = build_items(b);
+  if (st != PW_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return PW_OK;
+}
+
+pw_status pw_batch_run(pw_batch* b) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  int* cnt = reinterpret_cast<int*>(b->base + b->L.counters);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (2 * (size_t)b->n + 1), b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "resetting the batch counters");
+  int maxNN = 0;
+  for (const auto& d : b->inst) maxNN = d.slices > maxNN ? d.slices : maxNN;
+  dim3 tg((maxNN + 255) / 256, b->n);
+  pw::batch::batch_tables_kernel<<<tg, 256, 0, b->stream>>>(reinterpret_cast<const pw::TableArgs*>(b->base + b->L.targs));
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch tables launch");
+  pw::batch::Args g{};
+  g.inst = reinterpret_cast<const pw::batch::Inst*>(b->base + b->L.inst);
+  g.items = reinterpret_cast<const pw::batch::Item*>(b->base + b->L.items);
+  g.nitems = b->nitems;
+  g.pool = b->pool;
+  g.next = cnt + 2 * b->n;
+  g.doneA = cnt;
+  g.doneB = cnt + b->n;
+  g.err = cnt + 2 * b->n + 1;
+  g.wait_cycles = b->wait_cycles;
+  pw::batch::batch_kernel<<<num_sms(), pw::batch::NT, pw::batch::smem_bytes(), b->stream>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+  dim3 mg((maxNN + 255) / 256, b->n);
+  pw::batch::batch_mu_kernel<<<mg, 256, 0, b->stream>>>(g.inst, reinterpret_cast<float2* const*>(b->base + b->L.mu));
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch mu launch");
+  return PW_OK;
+}
+
+pw_status pw_batch_check(pw_batch* b) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  int flag = 0;
+  int* err = reinterpret_cast<int*>(b->base + b->L.counters) + 2 * b->n + 1;
+  cudaError_t e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the batch error flag");
+  if (flag) {
+    e = cudaMemsetAsync(err, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the batch error flag");
+    return fail(PW_ETIMEOUT, "a bounded wait of the batched launch gave up; some outputs are invalid");
+  }
+  return PW_OK;
+}
+
+pw_status pw_batch_set_chunk(pw_batch* b, int chunk) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  if (chunk < kMinChunk) return fail(PW_EINVAL, "chunk must be >= %d", kMinChunk);
+  b->chunk = chunk;
+  return build_items(b);
+}
+
+pw_status pw_batch_get_chunk(const pw_batch* b, int* chunk) {
+  pwi::set_last_error("");
+  if (!b || !chunk) return fail(PW_EINVAL, "null argument");
+  *chunk = b->chunk;
+  return PW_OK;
+}
+
+pw_status pw_batch_autotune(pw_batch* b, int* chunk_out) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  const int cand[] = {4, 8, 16, 32, 64};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "autotune events");
+  float best = 1e30f;
+  int best_c = b->chunk;
+  pw_status st = PW_OK;
+  for (int c : cand) {
+    if ((st = pw_batch_set_chunk(b, c)) != PW_OK) break;
+    if ((st = pw_batch_run(b)) != PW_OK) break;  // warm-up
+    cudaEventRecord(e0, b->stream);
+    if ((st = pw_batch_run(b)) != PW_OK) break;
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PW_OK) return st;
+  if ((st = pw_batch_check(b)) != PW_OK) return st;
+  if (chunk_out) *chunk_out = best_c;
+  return pw_batch_set_chunk(b, best_c);
+}
+
+pw_status pw_batch_inject_stall(pw_batch* b, int instance, double wait_s) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  if (instance < 0 || instance >= b->n) return fail(PW_EINVAL, "instance out of range");
+  if (!(wait_s > 0.0) || !std::isfinite(wait_s)) return fail(PW_EINVAL, "wait must be finite and > 0");
+  b->stalled[instance] = 1;
+  b->wait_cycles = (long long)(wait_s * 2.0e9);
+  return build_items(b);
+}
+
+pw_status pw_batch_destroy(pw_batch* b) {
+  pwi::set_last_error("");
+  if (!b) return PW_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  delete b;
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize in batch destroy");
+  return PW_OK;
+}
+
+}  // extern "C"

@@ -131,7 +131,8 @@ __device__ __forceinline__ void twiddle(float2* v, int j, const float2* tw) {
 //   JFAST = false: butterfly u -> line = u % N, j = u / N (lanes walk across lines)
 //   JFAST = true : butterfly u -> j = u % (N/R), line = u / (N/R) (lanes walk along a line)
 //   load(line, pos) -> float2, store(line, pos, float2); mid() runs between all loads and all
-//   stores (a barrier for an in-place stage on shared memory, or nothing).
+//   stores (a barrier for an in-place stage on shared memory, or nothing).  Threads with index
+//   >= NT (a block larger than the plan) take part in mid() only.
 template <int N, int R, int NS, int SIGN, bool JFAST, int NT, class Load, class Mid, class Store>
 __device__ __forceinline__ void fft_stage(const float2* tw, Load load, Mid mid, Store store) {
   static_assert(N % R == 0, "radix must divide N");

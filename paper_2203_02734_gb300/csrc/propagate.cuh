@@ -150,10 +150,10 @@ struct SmemFreeMid {
 
 // In-place shared-memory stages I..IEND-1 along AXIS (0: along the second index, element
 // (line, pos) at line*P + pos; 1: along the first index, element (pos, line) at pos*P + line).
-template <int N, int SIGN, int AXIS, int I, int IEND>
+template <int N, int SIGN, int AXIS, int I, int IEND, int NT = Plan<N>::NT>
 __device__ __forceinline__ void smem_stages(float2* buf, const float2* tw) {
   if constexpr (I < IEND) {
-    constexpr int P = pitch<N>(), NT = Plan<N>::NT;
+    constexpr int P = pitch<N>();
     constexpr int R = StageInfo<N, I>::R, NS = StageInfo<N, I>::NS;
     auto ld = [buf](int line, int pos) { return AXIS == 0 ? buf[line * P + pos] : buf[pos * P + line]; };
     auto st = [buf](int line, int pos, float2 v) {
@@ -161,7 +161,7 @@ __device__ __forceinline__ void smem_stages(float2* buf, const float2* tw) {
     };
     fft_stage<N, R, NS, SIGN, false, NT>(tw, ld, SyncMid{}, st);
     __syncthreads();
-    smem_stages<N, SIGN, AXIS, I + 1, IEND>(buf, tw);
+    smem_stages<N, SIGN, AXIS, I + 1, IEND, NT>(buf, tw);
   }
 }
 

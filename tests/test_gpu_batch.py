@@ -1,0 +1,135 @@
+"""Batched runs (many instances in one persistent launch) on the GPU: parity with the FP64
+oracle, repeatability, CUDA-graph replay, the autotuner, and the bounded dependency wait
+(a stalled instance yields PW_ETIMEOUT while the others complete)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+from gpu_cases import oracle_run, rel, source_mask
+
+pytestmark = pytest.mark.gpu
+
+DXI, LAM = 20e-6, 633e-9
+TOL = 1e-5
+
+
+def _mask(N, seed):
+    u = WL.uniform01(seed, 2 * N * N).reshape(2, N, N)
+    return (0.6 + 0.4 * u[0]) * np.exp(2j * np.pi * u[1])
+
+
+SPECS = [  # (N, z, farfield, lam, aperture, lens, with mask, full W)
+    (16, 0.4, 0, 633e-9, 0.12e-3, 0.25, True, True),
+    (32, 0.6, 1, 550e-9, 0.0, 0.0, False, False),
+    (64, 0.5, 0, 700e-9, 0.5e-3, 0.0, True, True),
+    (32, 1.5, 0, 600e-9, 0.3e-3, 0.4, False, True),
+]
+
+
+def _setup(torch, pw, stream=None):
+    insts, bufs, srcs = [], [], []
+    for k, (N, z, ff, lam, ap, lf, use_mask, full) in enumerate(SPECS):
+        m = WL.to_c64(_mask(N, 40 + k)) if use_mask else None
+        mt = torch.from_numpy(m).cuda() if use_mask else None
+        W = torch.empty((N,) * 4, dtype=torch.complex64, device="cuda") if full else None
+        S = torch.empty((N, N), dtype=torch.float32, device="cuda")
+        mu = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+        P1 = (N // 2 - 1, N // 2 + 1)
+        bufs.append((mt, W, S, mu))
+        insts.append(pw.pw_instance(N, DXI, lam, z, ff, 0.1e-3, 0.05e-3, 1.0 + 0.1 * k, ap, lf,
+                                    mt.data_ptr() if use_mask else None, P1[0], P1[1],
+                                    W.data_ptr() if full else None, S.data_ptr(), mu.data_ptr()))
+        srcs.append(dict(N=N, z=z, ff=ff, lam=lam, ap=ap, lf=lf, mask=m, A=1.0 + 0.1 * k, P1=P1, full=full))
+    nb = pw.pw_batch_workspace_bytes(insts, 2)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, s)
+    return b, bufs, srcs, ws
+
+
+def _oracle(src):
+    N = src["N"]
+    kind = "farfield" if src["ff"] else "fresnel"
+    W, _ = oracle_run(N, DXI, src["lam"], [(kind, src["z"])], gsm=(0.1e-3, 0.05e-3, src["A"]),
+                      aperture=src["ap"] or None, lens_f=src["lf"] or None, mask=src["mask"])
+    return W
+
+
+def _check(bufs, srcs):
+    errs = []
+    for (mt, W, S, mu), src in zip(bufs, srcs):
+        ref = _oracle(src)
+        Sref = np.real(O.spectral_density(ref))
+        muref = O.degree_of_coherence(ref, *src["P1"])
+        eS = rel(S.cpu().numpy(), Sref)
+        sel = Sref >= 1e-4 * Sref.max()
+        emu = rel(mu.cpu().numpy()[sel], muref[sel])
+        eW = rel(W.cpu().numpy(), ref) if W is not None else 0.0
+        errs.append((eW, eS, emu))
+        assert eS < TOL and emu < TOL and eW < TOL, (src["N"], eW, eS, emu)
+    return errs
+
+
+def test_batch_matches_oracle_and_repeats():
+    import torch
+    import paper_2203_02734_gb300 as pw
+    b, bufs, srcs, ws = _setup(torch, pw)
+    pw.pw_batch_run(b)
+    pw.pw_batch_check(b)
+    _check(bufs, srcs)
+    first = [S.clone() for (_, _, S, _) in bufs]
+    pw.pw_batch_run(b)
+    pw.pw_batch_check(b)
+    for f, (_, _, S, _) in zip(first, bufs):
+        assert torch.equal(f, S)
+    pw.pw_batch_destroy(b)
+
+
+def test_batch_graph_replay_and_autotune():
+    import torch
+    import paper_2203_02734_gb300 as pw
+    s = torch.cuda.Stream()
+    b, bufs, srcs, ws = _setup(torch, pw, stream=s)
+    chunk = pw.pw_batch_autotune(b)
+    assert chunk in (4, 8, 16, 32, 64) and pw.pw_batch_get_chunk(b) == chunk
+    with torch.cuda.stream(s):
+        pw.pw_batch_run(b)
+    s.synchronize()
+    for (_, _, S, _) in bufs:
+        S.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pw.pw_batch_run(b)
+    g.replay()
+    torch.cuda.synchronize()
+    pw.pw_batch_check(b)
+    _check(bufs, srcs)
+    pw.pw_batch_destroy(b)
+
+
+def test_batch_stalled_instance_times_out():
+    """Failure detection without a device fault: instance 1's pass-A work is left out on the host,
+    its pass-B work gives up after the bounded wait, the run reports PW_ETIMEOUT, and the other
+    instances are still correct."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    b, bufs, srcs, ws = _setup(torch, pw)
+    pw.pw_batch_inject_stall(b, 1, 0.2)
+    pw.pw_batch_run(b)
+    with pytest.raises(pw.PwError, match="PW_ETIMEOUT"):
+        pw.pw_batch_check(b)
+    pw.pw_batch_check(b)  # cleared
+    ok = [0, 2, 3]
+    _check([bufs[i] for i in ok], [srcs[i] for i in ok])
+    pw.pw_batch_destroy(b)
+
+
+def test_batch_rejects_bad_instances():
+    import torch
+    import paper_2203_02734_gb300 as pw
+    S = torch.empty((48, 48), dtype=torch.float32, device="cuda")
+    inst = [pw.pw_instance(48, DXI, LAM, 0.5, 0, 1e-4, 5e-5, 1.0, 0.0, 0.0, None, 0, 0, None, S.data_ptr(), None)]
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
+        pw.pw_batch_create(inst, 1, ws.data_ptr(), ws.numel())
