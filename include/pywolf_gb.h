@@ -129,6 +129,26 @@ pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask);
  * general (strided-store) second pass.  Read during the next propagation. */
 pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian);
 
+/* Delta-correlated (spatially incoherent) source W0 = weight d(xi1) delta(xi1 - xi2) with real
+ * d (N x N, device), the incoherent sources of Sec. 5.2 / 5.3 (delta-correlated CSD).  Recorded;
+ * generated inside the next propagation.  Also the adjoint source of an S-loss: if W_B = P(W0)
+ * and L depends on S_B = Re diag W_B, dL/dW_B* is this diagonal with d = dL/dS_B, weight = 1/2. */
+pw_status pw_source_diagonal(pw_csd* h, const float* dev_d, double weight);
+
+/* Parameter gradients from the adjoint (the paper has no counterpart; backward of a loss on S or
+ * on W through the propagation).  With W_B = P(W0) for the amplitude-masked GSM source
+ * W0 = A a(xi1) a(xi2) G (Sec. 5.4; a real N x N, dev_amask NULL for a = 1) propagated over z_m
+ * (farfield selects Eq. W_farfield), the adjoint P^H(Y) equals (d/dx)^4 conj(P'(conj Y)), where P'
+ * is the Fresnel propagation over the same z_m from the output sampling dx back onto the source
+ * grid d (times q(xi1) q*(xi2) in the far field).  Usage: on a handle whose current plane has
+ * sampling dx, set the conjugate of dL/dW_B* as its source (pw_source_diagonal for an S-loss),
+ * pw_propagate_fresnel(z_m), then call this: it reads the propagated CSDA (on grid d) and writes
+ * dev_grad3 = [dL/dsigma_S, dL/dsigma_mu, dL/dA] (3 doubles, device) and, if non-NULL,
+ * dev_grad_mask = dL/da (N x N float32, device); W0bar is never stored.  Asynchronous. */
+pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double amplitude,
+                          const float* dev_amask, double lambda_m, double z_m, int farfield,
+                          double* dev_grad3, float* dev_grad_mask);
+
 /* Fresnel propagation over distance z_m > 0 (Eq. W_fresnel; Algorithm 2 without the
  * far-field switch).  Result: dev_W holds W at the new plane, sampling lambda z/(N d);
  * S of the new plane is computed on the way.  Returns PW_ESTATE if no source was set. */

@@ -33,7 +33,7 @@ __all__ = [
     "apply_mask", "centred_dft2", "propagate_fft", "propagate_direct", "propagate_rows",
     "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
     "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
-    "propagate_rows_gsm",
+    "propagate_rows_gsm", "s_loss", "s_loss_gradient",
 ]
 
 
@@ -379,3 +379,43 @@ def gsm_beam_parameters(lam, z, sigma_S, sigma_mu):
     Delta = np.sqrt(1 + (z / (k * sigma_S * delta)) ** 2)
     Rz = z * (1 + (k * sigma_S * delta / z) ** 2)
     return Delta, Rz
+
+
+def s_loss(sigma_S, sigma_mu, A, amask, N, dxi, lam, z, S_target, weight, farfield=False):
+    """Least-squares loss on the propagated spectral density of the amplitude-masked GSM source
+    W0 = A a(xi1) a(xi2) G(xi1, xi2):  L = sum_x weight(x) (S_B(x) - S_target(x))^2."""
+    W0 = apply_mask(gsm_source(N, dxi, sigma_S, sigma_mu, A), amask)
+    WB, _ = propagate_fft(W0, dxi, lam, z, farfield)
+    S = np.real(spectral_density(WB))
+    return float(np.sum(weight * (S - S_target) ** 2)), S
+
+
+def s_loss_gradient(sigma_S, sigma_mu, A, amask, N, dxi, lam, z, S_target, weight, farfield=False):
+    """Gradient of s_loss by the adjoint: dL/dS = 2 weight (S - S_target); since S = Re W_B(x, x),
+    dL/dW_B* is the diagonal array (1/2) dL/dS; W0bar = P^H of it (propagate_adjoint); for each
+    real parameter theta, dL/dtheta = 2 Re sum conj(W0bar) dW0/dtheta with
+      dW0/dA = W0 / A,  dW0/dsigma_S = W0 (|xi1|^2 + |xi2|^2) / (2 sigma_S^3),
+      dW0/dsigma_mu = W0 |xi1 - xi2|^2 / sigma_mu^3,
+      dW0/da(eta) = A G (delta(xi1 = eta) a(xi2) + a(xi1) delta(xi2 = eta)).
+    Returns (L, dL/dsigma_S, dL/dsigma_mu, dL/dA, dL/da (N x N))."""
+    amask = np.asarray(amask, dtype=np.float64)
+    L, S = s_loss(sigma_S, sigma_mu, A, amask, N, dxi, lam, z, S_target, weight, farfield)
+    dLdS = 2.0 * weight * (S - S_target)
+    Ybar = np.zeros((N, N, N, N), dtype=np.complex128)
+    i = np.arange(N)
+    Ybar[i[:, None], i[None, :], i[:, None], i[None, :]] = 0.5 * dLdS
+    W0bar = propagate_adjoint(Ybar, dxi, lam, z, farfield)
+    G = gsm_source(N, dxi, sigma_S, sigma_mu, 1.0).real
+    W0 = A * amask[:, :, None, None] * amask[None, None, :, :] * G
+    x, y = axis_coords(N, dxi)
+    r2 = x[:, None] ** 2 + y[None, :] ** 2
+    R1 = r2[:, :, None, None]
+    R2 = r2[None, None, :, :]
+    D2 = (x[:, None, None, None] - x[None, None, :, None]) ** 2 + (y[None, :, None, None] - y[None, None, None, :]) ** 2
+    cW = np.conj(W0bar)
+    gA = 2.0 * np.real(np.sum(cW * W0 / A))
+    gS = 2.0 * np.real(np.sum(cW * W0 * (R1 + R2) / (2.0 * sigma_S ** 3)))
+    gM = 2.0 * np.real(np.sum(cW * W0 * D2 / sigma_mu ** 3))
+    AG = A * G
+    ga = 2.0 * np.real(np.einsum("abcd,abcd,cd->ab", cW, AG, amask) + np.einsum("abcd,abcd,ab->cd", cW, AG, amask))
+    return L, gS, gM, gA, ga

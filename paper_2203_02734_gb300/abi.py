@@ -39,6 +39,8 @@ SIGNATURES = {
     "pw_source_lens": (_i, [_vp, _d]),
     "pw_source_mask": (_i, [_vp, _vp]),
     "pw_source_array": (_i, [_vp, _vp, _i]),
+    "pw_source_diagonal": (_i, [_vp, _vp, _d]),
+    "pw_gsm_gradient": (_i, [_vp, _d, _d, _d, _vp, _d, _d, _i, _vp, _vp]),
     "pw_propagate_fresnel": (_i, [_vp, _d]),
     "pw_propagate_farfield": (_i, [_vp, _d]),
     "pw_get_sampling": (_i, [_vp, ctypes.POINTER(_d)]),
@@ -154,6 +156,16 @@ def pw_source_mask(h, dev_mask):
 
 def pw_source_array(h, dev_W0, hermitian=True):
     _check(LIB.pw_source_array(h, dev_W0, 1 if hermitian else 0))
+
+
+def pw_source_diagonal(h, dev_d, weight=1.0):
+    _check(LIB.pw_source_diagonal(h, dev_d, weight))
+
+
+def pw_gsm_gradient(h, sigma_S_m, sigma_mu_m, amplitude, dev_amask, lambda_m, z_m, farfield, dev_grad3,
+                    dev_grad_mask):
+    _check(LIB.pw_gsm_gradient(h, sigma_S_m, sigma_mu_m, amplitude, dev_amask, lambda_m, z_m, 1 if farfield else 0,
+                               dev_grad3, dev_grad_mask))
 
 
 def pw_propagate_fresnel(h, z_m):

@@ -231,6 +231,8 @@ pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool
     e = cudaMemcpyAsync(b->base + L.targs, targs.data(), sizeof(pw::TableArgs) * n, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->base + L.mu, mus.data(), sizeof(float2*) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)  // counters and the error flag start at zero (the workspace may hold old data)
+    e = cudaMemsetAsync(b->base + L.counters, 0, sizeof(int) * (2 * (size_t)n + 2), b->stream);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pw::batch::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)pw::batch::smem_bytes());
   if (e != cudaSuccess) {

@@ -107,10 +107,11 @@ __device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const
 // the uploaded W0 x factors), runs the 2D DFT (sign -1) with the rest of the cluster, and leaves
 // its 256 x 64 output tile (all c', d' in [64 r, 64 r + 64)) by one TMA tensor store
 // (box {2g floats, 1, 1, 64/g, 256}) into the V layout.
-template <bool ARRAY, bool MASK>
+template <int SRC, bool MASK>
 __global__ void __launch_bounds__(NT, 1)
     pass_a_d256(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
                 const float2* __restrict__ mask, int ap_ithr) {
+  constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
   extern __shared__ __align__(1024) float2 smem[];
   float2* slab = smem;  // RPC x N
   float2* tw = slab + RPC * N;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr int g = vgroup<N>();
   for (int ab = cluster; ab < N * N; ab += nclusters) {
     const int a = ab / N, b = ab - a * N;
-    if (!ARRAY) {
+    if (SRC == SRC_GSM) {
       for (int i = t; i < N; i += NT) {
         gA[i] = p.G[a * N + i];
         gB[i] = p.G[b * N + i];
@@ -144,20 +145,23 @@ __global__ void __launch_bounds__(NT, 1)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
-    if (!ARRAY) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
     float2 v[2][16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = RPC * (int)rank + rg + 32 * h;
-      const float2 sc = ARRAY ? cmul(s_ab, ein[c]) : cmul(s_ab, cscale(ein[c], gA[c]));
+      const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], gA[c])) : cmul(s_ab, ein[c]);
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int d = jq + 16 * r;
-        float2 x = cmul(sc, ARRAY ? ein[d] : cscale(ein[d], gB[d]));
+        float2 x = cmul(sc, SRC == SRC_GSM ? cscale(ein[d], gB[d]) : ein[d]);
         if (MASK) x = cmul(x, __ldg(mask + c * N + d));
         if (ARRAY) x = cmul(x, __ldg(W0 + (size_t)c * N + d));
-        v[h][r] = inside(c, d) ? x : make_float2(0.f, 0.f);
+        bool keep = inside(c, d);
+        if (DIAG) keep = keep && c == a && d == b;
+        v[h][r] = keep ? x : make_float2(0.f, 0.f);
       }
       Dft<16, -1>::run(v[h]);
     }

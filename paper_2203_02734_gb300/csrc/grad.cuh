@@ -1,0 +1,94 @@
+// grad.cuh -- parameter gradients of a loss through the propagation, from the adjoint.
+//
+// For W_B = P(W0) and a real loss L, the conjugate-Wirtinger gradient W0bar = dL/dW0* equals
+// P^H(dL/dW_B*), and P^H of a Fresnel propagation over z from sampling d is the conjugate of a
+// Fresnel propagation over the same z of the conjugated array, started from the output sampling
+// dx = lambda z/(N d) and scaled by (d/dx)^4 (the factorisation P = s D_out F D_in with
+// F^H = conj F).  The caller runs that forward propagation; its result R on the source grid gives
+// conj(W0bar) = c R (c = (d/dx)^4, times q(xi1) q*(xi2) for a far-field forward P).  This kernel
+// then forms, for the amplitude-masked GSM source W0 = A a(xi1) a(xi2) G(xi1, xi2) (Sec. 5.4),
+//   dL/dtheta = 2 Re sum conj(W0bar) dW0/dtheta   (theta = sigma_S, sigma_mu, A, a(eta)),
+// reading R once; W0 and dW0/dtheta are generated in registers.
+#pragma once
+#include "propagate.cuh"
+
+namespace pw {
+
+struct GradArgs {
+  int N;
+  double d;           // source sampling
+  double sigma_S, sigma_mu, A;
+  const float* amask; // N x N amplitude mask or nullptr (a = 1)
+  const float2* R;    // N^4 result of the adjoint propagation
+  double c;           // (d/dx)^4
+  int farfield;
+  double Kq;          // far field: q(xi) = exp(2 pi i Kq n^2) per axis, Kq = d^2/(2 lambda z)
+  double* g3;         // [dL/dsigma_S, dL/dsigma_mu, dL/dA] (accumulated; zeroed by the host)
+  float* gmask;       // N x N dL/da or nullptr
+};
+
+// One CTA per row eta = (ea, eb) of R; R is Hermitian, so the column sums of the mask gradient
+// equal the row sums and dL/da(eta) = 4 Re sum_xi2 conj(W0bar)(eta, xi2) A a(xi2) G(eta, xi2).
+__global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
+  extern __shared__ double gsm_sh[];
+  const int N = g.N, M = N / 2;
+  const int eta = blockIdx.x;
+  const int ea = eta / N, eb = eta - ea * N;
+  float* gx = reinterpret_cast<float*>(gsm_sh);  // G along the first axis for row ea
+  float* gy = gx + N;                            // G along the second axis for row eb
+  float2* qx = reinterpret_cast<float2*>(gy + N);  // far field: q(x_c) conj factors
+  double* red = reinterpret_cast<double*>(qx + 2 * N);
+  const double d = g.d;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double xa = (ea - M) * d, xi = (i - M) * d;
+    gx[i] = (float)exp(-(xa * xa + xi * xi) / (4 * g.sigma_S * g.sigma_S) - (xa - xi) * (xa - xi) / (2 * g.sigma_mu * g.sigma_mu));
+    const double yb = (M - eb) * d, yi = (M - i) * d;
+    gy[i] = (float)exp(-(yb * yb + yi * yi) / (4 * g.sigma_S * g.sigma_S) - (yb - yi) * (yb - yi) / (2 * g.sigma_mu * g.sigma_mu));
+    if (g.farfield) {
+      const double n2 = (double)(i - M) * (i - M);
+      qx[i] = cis_turns(frac_turns(n2 * g.Kq));
+    }
+  }
+  __syncthreads();
+  // conj(W0bar)(eta, xi2) = c R q(eta) q*(xi2) in the far field (q of both axes)
+  float2 qe = make_float2(1.f, 0.f);
+  if (g.farfield) qe = cmul(qx[ea], qx[eb]);
+  const float ae = g.amask ? g.amask[eta] : 1.f;
+  const double r2e = ((ea - M) * (ea - M) + (M - eb) * (M - eb)) * d * d;
+  double sS = 0, sM = 0, sA = 0, sa = 0;
+  const float2* Rrow = g.R + (size_t)eta * N * N;
+  for (int x = threadIdx.x; x < N * N; x += blockDim.x) {
+    const int c = x / N, e = x - c * N;
+    float2 r = __ldg(Rrow + x);
+    if (g.farfield) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
+    const double t = (double)r.x;  // dW0/dtheta is real: only Re(conj(W0bar)) enters
+    const double G = (double)gx[c] * (double)gy[e];
+    const double ax = g.amask ? (double)g.amask[x] : 1.0;
+    const double w0 = g.A * ae * ax * G;
+    const double r2x = ((c - M) * (c - M) + (M - e) * (M - e)) * d * d;
+    const double dx2 = ((ea - c) * (ea - c) + (eb - e) * (eb - e)) * d * d;
+    sS += t * w0 * (r2e + r2x);
+    sM += t * w0 * dx2;
+    sA += t * ae * ax * G;
+    sa += t * g.A * ax * G;
+  }
+  // block reduction of the four sums
+  double v[4] = {sS, sM, sA, sa};
+  for (int k = 0; k < 4; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[k * 8 + (threadIdx.x >> 5)] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x * 8 + w];
+    const double s3 = g.sigma_S * g.sigma_S * g.sigma_S, m3 = g.sigma_mu * g.sigma_mu * g.sigma_mu;
+    if (threadIdx.x == 0) atomicAdd(g.g3 + 0, 2.0 * g.c * x / (2.0 * s3));
+    if (threadIdx.x == 1) atomicAdd(g.g3 + 1, 2.0 * g.c * x / m3);
+    if (threadIdx.x == 2) atomicAdd(g.g3 + 2, 2.0 * g.c * x);
+    if (threadIdx.x == 3 && g.gmask) g.gmask[eta] = (float)(4.0 * g.c * x);
+  }
+}
+
+}  // namespace pw

@@ -84,12 +84,17 @@ static __global__ void tables_kernel(TableArgs t) {
   }
 }
 
+// Source of pass A: the GSM model, an uploaded CSDA, or a diagonal (delta-correlated,
+// incoherent) source W0 = w d(xi1) delta(xi1 - xi2), d real.
+enum SrcMode { SRC_GSM = 0, SRC_ARRAY = 1, SRC_DIAG = 2 };
+
 struct PassAArgs {
   const float2* F;
   const float* G;
   const float2* tw;
-  const float2* W0;  // uploaded source (ARRAY) or nullptr
-  float A;
+  const float2* W0;   // uploaded source (SRC_ARRAY) or nullptr
+  const float* diag;  // N x N diagonal (SRC_DIAG) or nullptr
+  float A;            // GSM amplitude, or the weight w of the diagonal source
 };
 
 template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
@@ -169,8 +174,9 @@ __device__ __forceinline__ void smem_stages(float2* buf, const float2* tw) {
 // Per slice: generate + DFT along c (lanes along d), DFT along d, write the natural-order slice
 // into shared memory and leave it by one TMA tensor store into the V layout (the 5D box
 // {2g floats, 1, 1, N/g, N} over (d' mod g, b, a, d'/g, c')).
-template <int N, bool ARRAY>
+template <int N, int SRC>
 __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_constant__ CUtensorMap vmap, PassAArgs p) {
+  constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
   constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
   extern __shared__ __align__(1024) float2 smem[];
   float2* buf = smem;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_con
   const float2* F = p.F;
   for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
     const int a = ab / N, b = ab - a * N;
-    if (!ARRAY) {
+    if (SRC == SRC_GSM) {
       for (int i = threadIdx.x; i < N; i += NT) {
         gA[i] = p.G[a * N + i];
         gB[i] = p.G[b * N + i];
@@ -189,11 +195,13 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_con
     }
     __syncthreads();
     float2 s_ab = cconj(__ldg(F + ab));
-    if (!ARRAY) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
     auto gen = [&](int d, int c) -> float2 {
       const float2 f = __ldg(F + c * N + d);
       if (ARRAY) return cmul(cmul(s_ab, __ldg(W0 + c * N + d)), f);
+      if (DIAG) return (c * N + d == ab) ? cmul(s_ab, f) : make_float2(0.f, 0.f);
       return cscale(cmul(s_ab, f), gA[c] * gB[d]);
     };
     auto st1 = [buf](int d, int c, float2 v) { buf[c * P + d] = v; };
@@ -282,12 +290,14 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
 // including masks recorded for this plane (W+ = conj(M0(x1)) W M0(x2)).
 struct SMuArgs {
   int N;
-  int mode;            // 0: GSM model, 1: CSDA in Wsrc (S from its diagonal), 2: CSDA + S in Sprop
+  int mode;            // 0: GSM model, 1: CSDA in Wsrc (S from its diagonal), 2: CSDA + S in Sprop,
+                       // 3: diagonal source A d(x)
   const float* G;
   float A;
   const float2* M0;    // nullptr = no mask
   const float2* Wsrc;
   const float* Sprop;
+  const float* diag;
   int iP, jP;
   float* S_out;        // nullptr = skip
   float2* mu_out;      // nullptr = skip
@@ -297,6 +307,7 @@ __device__ __forceinline__ float smu_S(const SMuArgs& a, int x) {
   const int N = a.N, i = x / N, j = x - i * N;
   float s;
   if (a.mode == 0) s = a.A * a.G[i * N + i] * a.G[j * N + j];
+  else if (a.mode == 3) s = a.A * a.diag[x];
   else if (a.mode == 2) s = a.Sprop[x];
   else s = a.Wsrc[(size_t)x * N * N + x].x;
   if (a.M0) {
@@ -318,6 +329,8 @@ static __global__ void s_mu_kernel(SMuArgs a) {
       float2 w;
       if (a.mode == 0) {
         w = make_float2(a.A * a.G[a.iP * N + i] * a.G[a.jP * N + j], 0.f);
+      } else if (a.mode == 3) {
+        w = make_float2(x == xp ? a.A * a.diag[x] : 0.f, 0.f);
       } else {
         w = a.Wsrc[(size_t)xp * NN + x];
       }

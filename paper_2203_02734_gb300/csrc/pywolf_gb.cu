@@ -14,6 +14,7 @@
 #include "../../include/pywolf_gb.h"
 #include "propagate.cuh"
 #include "d256.cuh"
+#include "grad.cuh"
 #include "r128.cuh"
 
 namespace {
@@ -37,7 +38,7 @@ pw_status cuda_fail(cudaError_t e, const char* what) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3 };
+enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3, SRC_DIAGONAL = 4 };
 
 }  // namespace
 
@@ -57,6 +58,7 @@ struct pw_csd {
   SourceKind kind;
   double sigma_S, sigma_mu, A;
   const pw_c32* W0;
+  const float* diag;  // diagonal source values (SRC_DIAGONAL)
   int hermitian;
   // masks of the current plane
   double aperture;  // <= 0: none
@@ -118,18 +120,18 @@ cudaError_t persistent_grid(K kernel, int threads, size_t smem, int slices, int*
   return cudaSuccess;
 }
 
-template <int N, bool ARRAY>
+template <int N, int SRC>
 cudaError_t launch_a(const CUtensorMap& vmap, const pw::PassAArgs& a, cudaStream_t s) {
   constexpr size_t smem = pw::pass_a_smem<N>();
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(pw::pass_a_kernel<N, ARRAY>,
+    cudaError_t e = cudaFuncSetAttribute(pw::pass_a_kernel<N, SRC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = persistent_grid(pw::pass_a_kernel<N, ARRAY>, pw::Plan<N>::NT, smem, N * N, &grid);
+    e = persistent_grid(pw::pass_a_kernel<N, SRC>, pw::Plan<N>::NT, smem, N * N, &grid);
     if (e != cudaSuccess) return e;
   }
-  pw::pass_a_kernel<N, ARRAY><<<grid, pw::Plan<N>::NT, smem, s>>>(vmap, a);
+  pw::pass_a_kernel<N, SRC><<<grid, pw::Plan<N>::NT, smem, s>>>(vmap, a);
   return cudaGetLastError();
 }
 
@@ -141,18 +143,18 @@ struct R128Extra {
   int* err;
 };
 
-template <bool ARRAY, bool MASK>
+template <int SRC, bool MASK>
 cudaError_t launch_a_r128(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   constexpr size_t smem = pw::r128::pass_a_smem();
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_a_r128<ARRAY, MASK>,
+    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_a_r128<SRC, MASK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = persistent_grid(pw::r128::pass_a_r128<ARRAY, MASK>, pw::r128::NT, smem, 128 * 128, &grid);
+    e = persistent_grid(pw::r128::pass_a_r128<SRC, MASK>, pw::r128::NT, smem, 128 * 128, &grid);
     if (e != cudaSuccess) return e;
   }
-  pw::r128::pass_a_r128<ARRAY, MASK><<<grid, pw::r128::NT, smem, s>>>(vmap, a, x.Ein, x.mask, x.ap_ithr);
+  pw::r128::pass_a_r128<SRC, MASK><<<grid, pw::r128::NT, smem, s>>>(vmap, a, x.Ein, x.mask, x.ap_ithr);
   return cudaGetLastError();
 }
 
@@ -199,10 +201,10 @@ cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* gri
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <bool ARRAY, bool MASK>
+template <int SRC, bool MASK>
 cudaError_t launch_a_d256(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   static int grid = 0;
-  return launch_clusters(pw::d256::pass_a_d256<ARRAY, MASK>, pw::d256::CS, pw::d256::NT, pw::d256::pass_a_smem(),
+  return launch_clusters(pw::d256::pass_a_d256<SRC, MASK>, pw::d256::CS, pw::d256::NT, pw::d256::pass_a_smem(),
                          &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr);
 }
 
@@ -227,20 +229,27 @@ cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
 }
 
 // ev: nullptr or three events recorded before pass A, between the passes and after pass B.
+// Pass A of the source mode `src` (pw::SrcMode) on the engine for N.
+template <int N, int SRC>
+cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
+  if constexpr (N == 128) {
+    return x.mask ? launch_a_r128<SRC, true>(vmap, a, x, s) : launch_a_r128<SRC, false>(vmap, a, x, s);
+  } else if constexpr (N == 256) {
+    return x.mask ? launch_a_d256<SRC, true>(vmap, a, x, s) : launch_a_d256<SRC, false>(vmap, a, x, s);
+  } else {
+    return launch_a<N, SRC>(vmap, a, s);
+  }
+}
+
+// ev: nullptr or three events recorded before pass A, between the passes and after pass B.
 template <int N>
-cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+cudaError_t launch_passes(int src, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
                           const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-  if constexpr (N == 128) {
-    if (x.mask) e = array ? launch_a_r128<true, true>(vmap, a, x, s) : launch_a_r128<false, true>(vmap, a, x, s);
-    else e = array ? launch_a_r128<true, false>(vmap, a, x, s) : launch_a_r128<false, false>(vmap, a, x, s);
-  } else if constexpr (N == 256) {
-    if (x.mask) e = array ? launch_a_d256<true, true>(vmap, a, x, s) : launch_a_d256<false, true>(vmap, a, x, s);
-    else e = array ? launch_a_d256<true, false>(vmap, a, x, s) : launch_a_d256<false, false>(vmap, a, x, s);
-  } else {
-    e = array ? launch_a<N, true>(vmap, a, s) : launch_a<N, false>(vmap, a, s);
-  }
+  if (src == pw::SRC_GSM) e = launch_a_mode<N, pw::SRC_GSM>(vmap, a, x, s);
+  else if (src == pw::SRC_DIAG) e = launch_a_mode<N, pw::SRC_DIAG>(vmap, a, x, s);
+  else e = launch_a_mode<N, pw::SRC_ARRAY>(vmap, a, x, s);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if constexpr (N == 128) {
@@ -255,12 +264,12 @@ cudaError_t launch_passes(bool array, bool herm, const CUtensorMap& vmap, const 
   return cudaSuccess;
 }
 
-cudaError_t dispatch(int N, bool array, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+cudaError_t dispatch(int N, int src, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
                      const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   switch (N) {
 #define PW_CASE(NN) \
   case NN:          \
-    return launch_passes<NN>(array, herm, vmap, a, b, x, s, ev);
+    return launch_passes<NN>(src, herm, vmap, a, b, x, s, ev);
     PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
     PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128) PW_CASE(256)
 #undef PW_CASE
@@ -350,18 +359,19 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
   if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
-  const bool herm = h->kind == SRC_GSM || h->hermitian != 0;
+  const bool herm = h->kind == SRC_GSM || h->kind == SRC_DIAGONAL || h->hermitian != 0;
   if (h->N == 256 && !herm)
     return fail(PW_EUNSUPPORTED, "N = 256 needs a Hermitian source (the general strided-store second pass "
                                  "exists for N <= 128 only)");
   pw_status st = build_tables(h, z, farfield);
   if (st != PW_OK) return st;
-  const bool array = h->kind != SRC_GSM;
+  const int src = h->kind == SRC_GSM ? pw::SRC_GSM : (h->kind == SRC_DIAGONAL ? pw::SRC_DIAG : pw::SRC_ARRAY);
   pw::PassAArgs a{};
   a.F = h->F;
   a.G = h->G;
   a.tw = h->tw;
-  a.W0 = array ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
+  a.W0 = src == pw::SRC_ARRAY ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
+  a.diag = h->diag;
   a.A = (float)h->A;
   pw::PassBArgs b{};
   b.V = reinterpret_cast<const float2*>(h->work);
@@ -383,13 +393,14 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
     const double thr = rp * rp;  // the FP64 threshold of the table kernel; r^2 is an integer
     x.ap_ithr = thr >= 2147483647.0 ? 2147483647 : (int)std::floor(thr);
   }
-  cudaError_t e = dispatch(h->N, array, herm, h->vmap, a, b, x, h->stream, ev);
+  cudaError_t e = dispatch(h->N, src, herm, h->vmap, a, b, x, h->stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
   // The output plane becomes the current plane; its CSDA is in W, its masks are unset.
   h->d = lz / (h->N * h->d);
   h->kind = SRC_PROPAGATED;
   h->hermitian = herm ? 1 : 0;
   h->W0 = nullptr;
+  h->diag = nullptr;
   h->aperture = 0.0;
   h->lens_f = 0.0;
   h->mask = nullptr;
@@ -405,7 +416,8 @@ pw_status s_mu(pw_csd* h, int iP, int jP, float* S, pw_c32* mu) {
   }
   pw::SMuArgs a{};
   a.N = h->N;
-  a.mode = h->kind == SRC_GSM ? 0 : (h->kind == SRC_ARRAY ? 1 : 2);
+  a.mode = h->kind == SRC_GSM ? 0 : (h->kind == SRC_ARRAY ? 1 : (h->kind == SRC_DIAGONAL ? 3 : 2));
+  a.diag = h->diag;
   a.G = h->G;
   a.A = (float)h->A;
   a.M0 = has_masks(h) ? h->M0 : nullptr;
@@ -657,6 +669,51 @@ pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian) {
   h->W0 = dev_W0;
   h->hermitian = hermitian ? 1 : 0;
   h->A = 1.0;
+  return PW_OK;
+}
+
+pw_status pw_source_diagonal(pw_csd* h, const float* dev_d, double weight) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (!dev_d) return fail(PW_EINVAL, "dev_d is null");
+  if (!std::isfinite(weight)) return fail(PW_EINVAL, "weight must be finite");
+  h->kind = SRC_DIAGONAL;
+  h->diag = dev_d;
+  h->W0 = nullptr;
+  h->A = weight;
+  return PW_OK;
+}
+
+pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double amplitude, const float* dev_amask,
+                          double lambda_m, double z_m, int farfield, double* dev_grad3, float* dev_grad_mask) {
+  g_err.clear();
+  if (!h || !dev_grad3) return fail(PW_EINVAL, "null argument");
+  if (!finite_pos(sigma_S_m) || !finite_pos(sigma_mu_m) || !finite_pos(lambda_m) || !finite_pos(z_m))
+    return fail(PW_EINVAL, "lengths must be finite and > 0");
+  if (!std::isfinite(amplitude)) return fail(PW_EINVAL, "amplitude must be finite");
+  if (h->kind != SRC_PROPAGATED) return fail(PW_ESTATE, "no propagated CSDA (run the adjoint propagation first)");
+  const int N = h->N;
+  const double d = h->d;                    // the source plane of the forward propagation
+  const double dx = lambda_m * z_m / (N * d);  // its output plane
+  pw::GradArgs g{};
+  g.N = N;
+  g.d = d;
+  g.sigma_S = sigma_S_m;
+  g.sigma_mu = sigma_mu_m;
+  g.A = amplitude;
+  g.amask = dev_amask;
+  g.R = reinterpret_cast<const float2*>(h->W);
+  g.c = std::pow(d / dx, 4);
+  g.farfield = farfield ? 1 : 0;
+  g.Kq = d * d / (2.0 * lambda_m * z_m);
+  g.g3 = dev_grad3;
+  g.gmask = dev_grad_mask;
+  cudaError_t e = cudaMemsetAsync(dev_grad3, 0, 3 * sizeof(double), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the gradient");
+  const size_t sh = 2 * N * sizeof(float) + 2 * N * sizeof(float2) + 32 * sizeof(double) + 64;
+  pw::gsm_gradient_kernel<<<N * N, 256, sh, h->stream>>>(g);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   return PW_OK;
 }
 

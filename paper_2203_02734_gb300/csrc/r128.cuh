@@ -105,10 +105,11 @@ __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][
 // G(b,d) (or W0 x factors) in registers, 2D DFT (sign -1) over (c, d), natural-order slice into
 // shared memory, one TMA tensor store into the V layout.  F(c, d) = Ein(c) Ein(d) Y(c, d) m(c, d)
 // from the per-axis factors, the aperture test and the optional mask.
-template <bool ARRAY, bool MASK>
+template <int SRC, bool MASK>
 __global__ void __launch_bounds__(NT, 1)
     pass_a_r128(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
                 const float2* __restrict__ mask, int ap_ithr) {
+  constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
   extern __shared__ __align__(1024) float2 smem[];
   float2* buf = smem;
   float2* tw = buf + N * N;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (inside(warp + 16 * rp, lane + 32 * rq)) inmask |= 1u << (rp * 4 + rq);
   for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
     const int a = ab / N, b = ab - a * N;
-    if (!ARRAY) {
+    if (SRC == SRC_GSM) {
       for (int i = t; i < N; i += NT) {
         gA[i] = p.G[a * N + i];
         gB[i] = p.G[b * N + i];
@@ -146,26 +147,29 @@ __global__ void __launch_bounds__(NT, 1)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
-    if (!ARRAY) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
     float2 ed[4];  // Ein(d) G(b, d)
 #pragma unroll
     for (int rq = 0; rq < 4; ++rq) {
       const int d = lane + 32 * rq;
-      ed[rq] = ARRAY ? ein[d] : cscale(ein[d], gB[d]);
+      ed[rq] = SRC == SRC_GSM ? cscale(ein[d], gB[d]) : ein[d];
     }
     float2 v[8][4];
 #pragma unroll
     for (int rp = 0; rp < 8; ++rp) {
       const int c = warp + 16 * rp;
-      const float2 sc = ARRAY ? cmul(s_ab, ein[c]) : cmul(s_ab, cscale(ein[c], gA[c]));
+      const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], gA[c])) : cmul(s_ab, ein[c]);
 #pragma unroll
       for (int rq = 0; rq < 4; ++rq) {
         const int d = lane + 32 * rq;
         float2 x = cmul(sc, ed[rq]);
         if (MASK) x = cmul(x, __ldg(mask + c * N + d));
         if (ARRAY) x = cmul(x, __ldg(W0 + c * N + d));
-        v[rp][rq] = (inmask >> (rp * 4 + rq)) & 1u ? x : make_float2(0.f, 0.f);
+        bool keep = (inmask >> (rp * 4 + rq)) & 1u;
+        if (DIAG) keep = keep && c == a && d == b;
+        v[rp][rq] = keep ? x : make_float2(0.f, 0.f);
       }
     }
     dft2d<8, 4, -1>(v);

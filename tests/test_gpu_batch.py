@@ -27,7 +27,7 @@ SPECS = [  # (N, z, farfield, lam, aperture, lens, with mask, full W)
 ]
 
 
-def _setup(torch, pw, stream=None):
+def _setup(torch, pw, stream=None, pool=2):
     insts, bufs, srcs = [], [], []
     for k, (N, z, ff, lam, ap, lf, use_mask, full) in enumerate(SPECS):
         m = WL.to_c64(_mask(N, 40 + k)) if use_mask else None
@@ -41,10 +41,10 @@ def _setup(torch, pw, stream=None):
                                     mt.data_ptr() if use_mask else None, P1[0], P1[1],
                                     W.data_ptr() if full else None, S.data_ptr(), mu.data_ptr()))
         srcs.append(dict(N=N, z=z, ff=ff, lam=lam, ap=ap, lf=lf, mask=m, A=1.0 + 0.1 * k, P1=P1, full=full))
-    nb = pw.pw_batch_workspace_bytes(insts, 2)
-    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    nb = pw.pw_batch_workspace_bytes(insts, pool)
+    ws = torch.full((nb,), 0xAB, dtype=torch.uint8, device="cuda")  # stale bytes must not matter
     s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
-    b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, s)
+    b = pw.pw_batch_create(insts, pool, ws.data_ptr(), nb, s)
     return b, bufs, srcs, ws
 
 
@@ -114,7 +114,8 @@ def test_batch_stalled_instance_times_out():
     instances are still correct."""
     import torch
     import paper_2203_02734_gb300 as pw
-    b, bufs, srcs, ws = _setup(torch, pw)
+    # a pool slot per instance: no other instance waits on the stalled one's buffer
+    b, bufs, srcs, ws = _setup(torch, pw, pool=len(SPECS))
     pw.pw_batch_inject_stall(b, 1, 0.2)
     pw.pw_batch_run(b)
     with pytest.raises(pw.PwError, match="PW_ETIMEOUT"):

@@ -296,3 +296,30 @@ def test_golden_paper_numbers():
 def test_odd_n_rejected():
     with pytest.raises(ValueError):
         O.axis_coords(7, DXI)
+
+
+# --------------------------------------------------------------------------- gradients
+@pytest.mark.parametrize("farfield", [False, True])
+def test_s_loss_gradient_matches_central_differences(farfield):
+    """Adjoint gradient of the S loss vs central finite differences (FP64), for sigma_S, sigma_mu,
+    the amplitude A and two mask pixels."""
+    N, z, lam = 8, 0.6, 633e-9
+    rng = np.random.default_rng(2)
+    amask = 0.5 + 0.5 * rng.random((N, N))
+    target = O.s_loss(1.2 * SS, 0.8 * SM, 1.1, 0.7 + 0.3 * rng.random((N, N)), N, DXI, lam, z,
+                      np.zeros((N, N)), np.ones((N, N)), farfield)[1]
+    weight = 1.0 + rng.random((N, N))
+    L, gS, gM, gA, ga = O.s_loss_gradient(SS, SM, 1.0, amask, N, DXI, lam, z, target, weight, farfield)
+
+    def f(sS=SS, sM=SM, A=1.0, am=amask):
+        return O.s_loss(sS, sM, A, am, N, DXI, lam, z, target, weight, farfield)[0]
+    h = 1e-6
+    assert abs((f(sS=SS * (1 + h)) - f(sS=SS * (1 - h))) / (2 * h * SS) - gS) < 1e-6 * abs(gS)
+    assert abs((f(sM=SM * (1 + h)) - f(sM=SM * (1 - h))) / (2 * h * SM) - gM) < 1e-6 * abs(gM)
+    assert abs((f(A=1 + h) - f(A=1 - h)) / (2 * h) - gA) < 1e-6 * abs(gA)
+    for (a, b) in [(3, 4), (0, 7)]:
+        ap, am_ = amask.copy(), amask.copy()
+        ap[a, b] += h
+        am_[a, b] -= h
+        fd = (f(am=ap) - f(am=am_)) / (2 * h)
+        assert abs(fd - ga[a, b]) < 1e-6 * np.abs(ga).max()
