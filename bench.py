@@ -37,7 +37,8 @@ import workloads as WL  # noqa: E402
 
 WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
              WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256,
-             WL.POLYCHROMATIC_BATCH["name"]: WL.POLYCHROMATIC_BATCH}
+             WL.POLYCHROMATIC_BATCH["name"]: WL.POLYCHROMATIC_BATCH,
+             WL.INVERSE_N96["name"]: WL.INVERSE_N96}
 DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
 CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
@@ -467,11 +468,68 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Differentiable workload (N = 96, z = 1 m, amplitude-masked GSM): one step = forward S and the
+    backward pass of a least-squares S loss through the hand-written adjoint (gradients for sigma_S,
+    sigma_mu, A and the N x N mask); reported next to the forward alone (the plain path)."""
+    import torch
+    from paper_2203_02734_gb300.autograd import GSMIntensity
+
+    torch.cuda.set_device(0)
+    N = CFG["N"]
+    model = GSMIntensity(N, CFG["dxi"], CFG["lam"], CFG["z"])
+    am = torch.tensor(WL.amplitude_mask(N).real, dtype=torch.float32, device="cuda", requires_grad=True)
+    sS = torch.tensor(CFG["sigma_S"], dtype=torch.float64, requires_grad=True)
+    sM = torch.tensor(CFG["sigma_mu"], dtype=torch.float64, requires_grad=True)
+    A = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    with torch.no_grad():
+        target = model(sS * 1.2, sM * 0.8, A, am * 0.9).double()
+
+    def fwd_bwd():
+        S = model(sS, sM, A, am)
+        L = torch.sum((S.double() - target) ** 2)
+        L.backward()
+
+    def fwd():
+        with torch.no_grad():
+            model(sS, sM, A, am)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps
+
+    clock = ClockSampler(torch.cuda.current_device())
+    t0 = time.time()
+    t_fb = timed(fwd_bwd, args.steps)
+    t1 = time.time()
+    clocks = clock.stop(t0, t1)
+    t_f = timed(fwd, args.steps)
+    model.close()
+    pts = N ** 4
+    line = {"metric": METRIC, "value": pts / t_fb, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_fb, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CFG["name"], "N": N, "z_m": CFG["z"], "points_per_step": pts,
+                       "step": "forward S + backward of a least-squares S loss (hand-written adjoint)"},
+            "plain_path": {"value": pts / t_f, "unit": UNIT, "ms_per_step": 1e3 * t_f,
+                           "what": "the forward propagation + S alone"},
+            "gpu_launches": 7 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
     elif CFG is WL.POLYCHROMATIC_BATCH:
         run_batch(a)
+    elif CFG is WL.INVERSE_N96:
+        run_adjoint(a)
     else:
         run_ours(a)

@@ -54,26 +54,39 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   float2 qe = make_float2(1.f, 0.f);
   if (g.farfield) qe = cmul(qx[ea], qx[eb]);
   const float ae = g.amask ? g.amask[eta] : 1.f;
-  const double r2e = ((ea - M) * (ea - M) + (M - eb) * (M - eb)) * d * d;
-  double sS = 0, sM = 0, sA = 0, sa = 0;
+  const float d2 = (float)(d * d);
+  const float r2e = (float)((ea - M) * (ea - M) + (M - eb) * (M - eb));  // in units of d^2
+  // per-thread partial sums in FP32 (each thread adds N^2 / blockDim terms), reduced in FP64
+  float sS = 0.f, sM = 0.f, sA = 0.f, sa = 0.f;
   const float2* Rrow = g.R + (size_t)eta * N * N;
-  for (int x = threadIdx.x; x < N * N; x += blockDim.x) {
-    const int c = x / N, e = x - c * N;
+  const int NN = N * N, step = blockDim.x, dc = step / N, de = step - dc * N;
+  int c = threadIdx.x / N, e = threadIdx.x - c * N;
+  for (int x = threadIdx.x; x < NN; x += step) {
     float2 r = __ldg(Rrow + x);
     if (g.farfield) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
-    const double t = (double)r.x;  // dW0/dtheta is real: only Re(conj(W0bar)) enters
-    const double G = (double)gx[c] * (double)gy[e];
-    const double ax = g.amask ? (double)g.amask[x] : 1.0;
-    const double w0 = g.A * ae * ax * G;
-    const double r2x = ((c - M) * (c - M) + (M - e) * (M - e)) * d * d;
-    const double dx2 = ((ea - c) * (ea - c) + (eb - e) * (eb - e)) * d * d;
-    sS += t * w0 * (r2e + r2x);
-    sM += t * w0 * dx2;
-    sA += t * ae * ax * G;
-    sa += t * g.A * ax * G;
+    const float t = r.x;  // dW0/dtheta is real: only Re(conj(W0bar)) enters
+    const float G = gx[c] * gy[e];
+    const float ax = g.amask ? __ldg(g.amask + x) : 1.f;
+    const float tG = t * ax * G;
+    const float r2x = (float)((c - M) * (c - M) + (M - e) * (M - e));
+    const float dx2 = (float)((ea - c) * (ea - c) + (eb - e) * (eb - e));
+    sS = fmaf(tG, r2e + r2x, sS);
+    sM = fmaf(tG, dx2, sM);
+    sA += tG;
+    e += de;
+    c += dc;
+    if (e >= N) {
+      e -= N;
+      ++c;
+    }
   }
+  // the mask-gradient sum is A * sA; the others scale with w0 = A a(eta) a(xi2) G
+  sa = sA;
+  sS *= ae * d2;
+  sM *= ae * d2;
+  sA *= ae;
   // block reduction of the four sums
-  double v[4] = {sS, sM, sA, sa};
+  double v[4] = {(double)sS, (double)sM, (double)sA, (double)sa};
   for (int k = 0; k < 4; ++k) {
     double x = v[k];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -84,10 +97,11 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
     double x = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x * 8 + w];
     const double s3 = g.sigma_S * g.sigma_S * g.sigma_S, m3 = g.sigma_mu * g.sigma_mu * g.sigma_mu;
-    if (threadIdx.x == 0) atomicAdd(g.g3 + 0, 2.0 * g.c * x / (2.0 * s3));
-    if (threadIdx.x == 1) atomicAdd(g.g3 + 1, 2.0 * g.c * x / m3);
+    // sS, sM carry a(eta) a(xi2) G t (r^2 terms), sA carries a(eta) a(xi2) G t, sa carries a(xi2) G t
+    if (threadIdx.x == 0) atomicAdd(g.g3 + 0, 2.0 * g.c * g.A * x / (2.0 * s3));
+    if (threadIdx.x == 1) atomicAdd(g.g3 + 1, 2.0 * g.c * g.A * x / m3);
     if (threadIdx.x == 2) atomicAdd(g.g3 + 2, 2.0 * g.c * x);
-    if (threadIdx.x == 3 && g.gmask) g.gmask[eta] = (float)(4.0 * g.c * x);
+    if (threadIdx.x == 3 && g.gmask) g.gmask[eta] = (float)(4.0 * g.c * g.A * x);
   }
 }
 
