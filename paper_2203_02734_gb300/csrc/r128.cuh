@@ -340,6 +340,16 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
         cp_async8(stg + a * N + b, Vg + (size_t)(a * N + b) * g);
       }
   };
+  // The four columns d' = 4 (d'/4) + j of one (c', d'/4) share one 512 KB block of V; the CTA of
+  // column j brings quarter j of the block of the column after next into L2, so that the gathers
+  // (8 bytes from every 32-byte sector) hit L2 instead of waiting on DRAM.
+  auto prefetch = [&](int cdn) {
+    if (t == 0 && cdn < N * N) {
+      const int cn = cdn / N, dn = cdn % N;
+      bulk_prefetch_l2(p.V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * N * N, (unsigned)(N * N * sizeof(float2)));
+    }
+  };
+  prefetch(blockIdx.x + gridDim.x);
   if (blockIdx.x < N * N) gather(blockIdx.x);
   cp_async_commit();
   __syncthreads();  // tw, eo
@@ -354,6 +364,7 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
     dft2d<8, 4, +1>(v);  // consumes every staged value before the tile is refilled
     if (cd + (int)gridDim.x < N * N) gather(cd + gridDim.x);
     cp_async_commit();
+    prefetch(cd + 2 * gridDim.x);
     float2 w3[2][4][4];
     stages_23_half<+1>(v, w3, xb, tw);
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
