@@ -19,7 +19,6 @@ per step ("scaling": "weak"); time is the maximum over ranks.
 cores, each step one oracle propagation of the same configuration on an N = 64 grid.
 """
 import argparse
-import glob
 import hashlib
 import json
 import os
@@ -136,10 +135,10 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU helpers
 def kernel_source_sha():
-    """Hash of the device-code headers of the two passes (fft.cuh, propagate.cuh)."""
+    """Hash of the device-code headers the N = 128 pass kernels are built from."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2203_02734_gb300", "csrc", "*.cuh"))):
-        h.update(open(p, "rb").read())
+    for name in ("cluster.cuh", "fft.cuh", "propagate.cuh", "r128.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_02734_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
