@@ -9,8 +9,7 @@ Notation follows the paper:
   * the propagator is q(R, xi) = exp(i pi |xi|^2 / (lambda R))          (Eq. q_factor);
   * the output sampling is dx = lambda R / (N dxi)                      (Eq. spatial_resolution).
 
-Readings of passages that are garbled, ambiguous or silent (each one is listed in
-the design doc with its justification):
+Readings of passages that are garbled, ambiguous or silent:
   R1  GSM source: W = A exp(-(|xi1|^2+|xi2|^2)/(4 sigma_S^2)) exp(-|xi1-xi2|^2/(2 sigma_mu^2))
       (Sec. 5.4; the printed exponents lost their minus signs).
   R2  Circular aperture: the product Y(xi1) Y(xi2) of the text (appendix), boundary
