@@ -101,7 +101,10 @@ template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
 // Width g of the d' runs of the V layout: 4 (one 32-byte sector per run; 2 when 4 does not
 // divide N).  Narrower 16-byte runs halve pass B's gather traffic but make pass A's TMA store
 // issue twice as many half-sector writes, which costs more than it saves (measured at N = 128).
-__host__ __device__ constexpr int vgroup_of(int n) { return n % 4 == 0 ? 4 : 2; }
+// g = 4 makes each run one 32-byte sector.  N = 256 uses g = 8: its pass A leaves each 128 KB
+// output tile by TMA between two uses of the same shared buffer, and the store of 64-byte runs
+// drains in half the time (pass B's 8-byte gathers cost about the same either way).
+__host__ __device__ constexpr int vgroup_of(int n) { return n == 256 ? 8 : n % 4 == 0 ? 4 : 2; }
 template <int N> __host__ __device__ constexpr int vgroup() { return vgroup_of(N); }
 // offset of V(a, b, c', d') in the V layout
 template <int N>
