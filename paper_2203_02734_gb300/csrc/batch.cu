@@ -1,6 +1,7 @@
 // batch.cu -- C ABI of the batched run (pw_batch_*): instance descriptors, workspace layout,
 // item list, launch sequence (counter reset, FP64 tables, one persistent launch, mu) and the
 // chunk-size autotuner.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -12,7 +13,8 @@
 #include "batch.cuh"
 
 namespace pwi {
-void set_last_error(const char* msg);  // pywolf_gb.cu
+void set_last_error(const char* msg);                        // pywolf_gb.cu
+pw_status encode_vmap(CUtensorMap* map, void* work, int N);  // pywolf_gb.cu
 }
 
 namespace {
@@ -40,7 +42,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout (offsets from the base, each part 256-byte aligned).
 struct Layout {
-  size_t inst, targs, mu, items, counters, tables, pool, total;
+  size_t inst, targs, mu, items, counters, tmaps, tables, pool, total;
   int max_items;
   size_t slot_bytes;
 };
@@ -68,6 +70,8 @@ Layout layout(const pw_instance* in, int n, int pool) {
   off = align256(off + sizeof(pw::batch::Item) * items);
   L.counters = off;
   off = align256(off + sizeof(int) * (2 * (size_t)n + 2));
+  L.tmaps = off;  // one tensor map per pool slot (N = 128 instances store V by TMA)
+  off = align256(off + sizeof(CUtensorMap) * pool);
   L.tables = off;
   for (int i = 0; i < n; ++i) {
     const size_t N = in[i].N, NN = N * N;
@@ -75,6 +79,7 @@ Layout layout(const pw_instance* in, int n, int pool) {
     off = align256(off + NN * sizeof(float));   // G
     off = align256(off + N * sizeof(float2));   // twiddles
     off = align256(off + N * sizeof(float2));   // output propagators
+    off = align256(off + N * sizeof(float2));   // per-axis input factors
     off = align256(off + NN * sizeof(float2));  // W(P1, .)
   }
   L.pool = off;
@@ -101,18 +106,29 @@ namespace {
 
 pw_status build_items(pw_batch* b) {
   std::vector<pw::batch::Item> items;
+  // One pass = J = ceil(S / chunk) items.  N = 128 (register-resident engine, whose pass B
+  // gathers 8 bytes from every 32-byte run of V): strided items, item j takes slices j, j + J,
+  // j + 2 J, ..., so that neighbouring CTAs gather the columns of one run together.  Other sizes:
+  // contiguous ranges of chunk slices (measured slightly faster there).
   auto add = [&](int i, int pass) {
     if (pass == 0 && b->stalled[i]) return;
-    const int s = b->inst[i].slices;
-    for (int s0 = 0; s0 < s; s0 += b->chunk) items.push_back({i, pass, s0, s0 + b->chunk < s ? s0 + b->chunk : s});
+    const int S = b->inst[i].slices;
+    const int J = (S + b->chunk - 1) / b->chunk;
+    for (int j = 0; j < J; ++j) {
+      if (b->inst[i].N == 128) items.push_back({i, pass, j, (S - j + J - 1) / J, J});
+      else items.push_back({i, pass, j * b->chunk, j + 1 < J ? b->chunk : S - j * b->chunk, 1});
+    }
   };
-  // one-instance lookahead: A(0), A(1), B(0), A(2), B(1), ..., B(n-1)
-  add(0, 0);
-  for (int i = 1; i < b->n; ++i) {
-    add(i, 0);
-    add(i - 1, 1);
+  // Lookahead of L instances: A(0) .. A(L-1), then B(i), A(i + L) for i = 0, 1, ...  B(i) waits
+  // for A(i), listed L phases earlier; A(i + L) reuses the slot of instance i + L - pool and waits
+  // for its pass B, listed pool - L phases earlier.  L = pool - 2 (at least 1) leaves two phases
+  // between every wait and the items it waits on, and every awaited item precedes its waiter.
+  const int L = b->pool >= 3 ? b->pool - 2 : 1;
+  for (int i = 0; i < L && i < b->n; ++i) add(i, 0);
+  for (int i = 0; i < b->n; ++i) {
+    add(i, 1);
+    if (i + L < b->n) add(i + L, 0);
   }
-  add(b->n - 1, 1);
   if ((int)items.size() > b->L.max_items) return fail(PW_EINVAL, "item list exceeds the workspace");
   b->nitems = (int)items.size();
   cudaError_t e = cudaMemcpyAsync(b->base + b->L.items, items.data(), items.size() * sizeof(pw::batch::Item),
@@ -192,13 +208,18 @@ pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool
     off = align256(off + N * sizeof(float2));
     float2* Eo = reinterpret_cast<float2*>(b->base + off);
     off = align256(off + N * sizeof(float2));
+    float2* Ei = reinterpret_cast<float2*>(b->base + off);
+    off = align256(off + N * sizeof(float2));
     d.row = reinterpret_cast<float2*>(b->base + off);
     off = align256(off + NN * sizeof(float2));
     d.F = F;
     d.G = G;
     d.tw = tw;
     d.Eout = Eo;
+    d.Ein = Ei;
+    d.mask = reinterpret_cast<const float2*>(q.dev_mask);
     d.V = reinterpret_cast<float2*>(b->base + L.pool + L.slot_bytes * (i % pool));
+    d.vmap = N == 128 ? b->base + L.tmaps + sizeof(CUtensorMap) * (i % pool) : nullptr;
     d.W = reinterpret_cast<float2*>(q.dev_W);
     d.S = q.dev_S;
     mus[i] = reinterpret_cast<float2*>(q.dev_mu);
@@ -215,18 +236,36 @@ pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool
     t.gm = q.dxi_m * q.dxi_m / (2.0 * q.sigma_mu_m * q.sigma_mu_m);
     if (q.aperture_m > 0.0) {
       const double rp = q.aperture_m / q.dxi_m;
-      t.ap_thr = rp * rp;
+      t.ap_thr = rp * rp;  // r^2 is an integer: the integer floor gives the same decision
+      d.ap_ithr = t.ap_thr >= 2147483647.0 ? 2147483647 : (int)std::floor(t.ap_thr);
     } else {
       t.ap_thr = -1.0;
+      d.ap_ithr = -1;
     }
     t.mask = reinterpret_cast<const float2*>(q.dev_mask);
     t.F = F;
     t.G = G;
     t.tw = tw;
     t.Eout = Eo;
+    t.Ein = Ei;
+  }
+  bool any128 = false;
+  for (int i = 0; i < n; ++i) any128 = any128 || in[i].N == 128;
+  std::vector<CUtensorMap> maps(pool);
+  if (any128) {
+    for (int k = 0; k < pool; ++k) {
+      pw_status st = pwi::encode_vmap(&maps[k], b->base + L.pool + L.slot_bytes * k, 128);
+      if (st != PW_OK) {
+        delete b;
+        return st;
+      }
+    }
   }
   cudaError_t e = cudaMemcpyAsync(b->base + L.inst, b->inst.data(), sizeof(pw::batch::Inst) * n,
                                   cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && any128)
+    e = cudaMemcpyAsync(b->base + L.tmaps, maps.data(), sizeof(CUtensorMap) * pool, cudaMemcpyHostToDevice,
+                        b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->base + L.targs, targs.data(), sizeof(pw::TableArgs) * n, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)

@@ -166,6 +166,29 @@ __device__ __forceinline__ void fft_stage(const float2* tw, Load load, Mid mid, 
   }
 }
 
+// The same stage out of place, one butterfly at a time: load(line, pos) must not read what
+// store(line, pos, v) writes.  Only the R values of the current butterfly are live, so a block
+// larger than its register budget allows for fft_stage still runs without spills.
+template <int N, int R, int NS, int SIGN, bool JFAST, int NT, class Load, class Store>
+__device__ __forceinline__ void fft_stage_stream(const float2* tw, Load load, Store store) {
+  static_assert(N % R == 0, "radix must divide N");
+  constexpr int NJ = N / R;
+  constexpr int NB = N * NJ;
+#pragma unroll 1
+  for (int u = threadIdx.x; u < NB; u += NT) {
+    const int line = JFAST ? u / NJ : u % N;
+    const int j = JFAST ? u % NJ : u / N;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = load(line, j + r * NJ);
+    twiddle<N, R, NS, SIGN>(v, j, tw);
+    Dft<R, SIGN>::run(v);
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) store(line, base + r * NS, v[r]);
+  }
+}
+
 struct SyncMid {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };

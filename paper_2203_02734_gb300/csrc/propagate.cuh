@@ -124,6 +124,11 @@ template <int N> __host__ __device__ constexpr size_t pass_b_smem() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Orders this thread's completed async-proxy writes to global memory (bulk / tensor stores)
+// before its later generic-proxy operations (a release that publishes them).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // wait until every committed bulk copy of this thread has finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read_all() {

@@ -45,6 +45,7 @@ enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3, 
 namespace pwi {
 // Sets the thread's message returned by pw_last_error() (used by other translation units).
 void set_last_error(const char* msg) { g_err = msg; }
+pw_status encode_vmap(CUtensorMap* map, void* work, int N);
 }  // namespace pwi
 
 struct pw_csd {
@@ -292,26 +293,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// 5D map of the work buffer in the V layout, as 32-bit floats: dims (innermost first)
-// (2g floats of one d' run, b, a, d'/g, c'); box = one whole slice {2g, 1, 1, N/g, N}.
-pw_status make_vmap(pw_csd* h) {
-  const int N = h->N;
-  const int g = pw::vgroup_of(N);
-  auto enc = encode_tiled();
-  if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-  const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
-  cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
-  cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
-  // N = 256: each CTA of a cluster stores a tile of N / 4 columns (d256.cuh)
-  const int cols = N == 256 ? N / pw::d256::CS : N;
-  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)N};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  CUresult r = enc(&h->vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)h->work, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
-  return PW_OK;
-}
+pw_status make_vmap(pw_csd* h) { return pwi::encode_vmap(&h->vmap, h->work, h->N); }
 
 // Fill F, M0, G, tw, Eout for a propagation over z (z <= 0: source-plane view only).
 pw_status build_tables(pw_csd* h, double z, bool farfield) {
@@ -435,6 +417,28 @@ pw_status s_mu(pw_csd* h, int iP, int jP, float* S, pw_c32* mu) {
 }
 
 }  // namespace
+
+namespace pwi {
+// 5D map of a work buffer in the V layout, as 32-bit floats: dims (innermost first)
+// (2g floats of one d' run, b, a, d'/g, c'); box = one whole slice {2g, 1, 1, N/g, N}
+// (N = 256: each CTA of a cluster stores a tile of N / 4 columns, d256.cuh).
+pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
+  const int g = pw::vgroup_of(N);
+  auto enc = encode_tiled();
+  if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
+  cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
+  cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
+  const int cols = N == 256 ? N / pw::d256::CS : N;
+  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)N};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, work, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return PW_OK;
+}
+}  // namespace pwi
 
 extern "C" {
 

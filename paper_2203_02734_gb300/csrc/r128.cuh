@@ -318,7 +318,7 @@ constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(f
 // runs in registers (stages_23_half through a 64 KB exchange buffer), and the epilogue (scale,
 // output propagators, S on the diagonal) writes the conjugated column as the contiguous row
 // W(c', d', ., .) straight from registers (Hermitian store).
-__global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
+static __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
   extern __shared__ __align__(1024) float2 smem[];
   float2* stg = smem;
   float2* xb = stg + N * N;

@@ -134,3 +134,46 @@ def test_batch_rejects_bad_instances():
     ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
         pw.pw_batch_create(inst, 1, ws.data_ptr(), ws.numel())
+
+
+def test_batch_mixes_register_engine_n128():
+    """An N = 128 instance (register-resident engine: TMA-stored slices, gathered columns) in the
+    same launch as an N = 64 one, run twice.  The N = 128 GSM source behind a thin lens is
+    separable, so the oracle's per-axis quadrature gives its exact propagated CSDA."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    N1, z1, lam1, lf1, A1 = 128, 0.5, 600e-9, 0.4, 1.2
+    N2, z2, lam2 = 64, 0.7, 650e-9
+    W1 = torch.empty((N1,) * 4, dtype=torch.complex64, device="cuda")
+    S1 = torch.empty((N1, N1), dtype=torch.float32, device="cuda")
+    mu1 = torch.empty((N1, N1), dtype=torch.complex64, device="cuda")
+    m2 = WL.to_c64(_mask(N2, 77))
+    m2t = torch.from_numpy(m2).cuda()
+    S2 = torch.empty((N2, N2), dtype=torch.float32, device="cuda")
+    mu2 = torch.empty((N2, N2), dtype=torch.complex64, device="cuda")
+    P1 = (N1 // 2, N1 // 2 - 3)
+    insts = [pw.pw_instance(N1, DXI, lam1, z1, 0, 0.1e-3, 0.05e-3, A1, 0.0, lf1, None, P1[0], P1[1],
+                            W1.data_ptr(), S1.data_ptr(), mu1.data_ptr()),
+             pw.pw_instance(N2, DXI, lam2, z2, 0, 0.1e-3, 0.05e-3, 1.0, 0.45e-3, 0.0, m2t.data_ptr(), 30, 33,
+                            None, S2.data_ptr(), mu2.data_ptr())]
+    nb = pw.pw_batch_workspace_bytes(insts, 2)
+    ws = torch.full((nb,), 0xAB, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, torch.cuda.current_stream().cuda_stream)
+    for rep in range(2):
+        S1.zero_()
+        pw.pw_batch_run(b)
+        pw.pw_batch_check(b)
+        torch.cuda.synchronize()
+        ref = O.gsm_separable_quadrature(N1, DXI, lam1, z1, 0.1e-3, 0.05e-3, A1, lens_f=lf1)
+        for (a, c) in [P1, (60, 70), (70, 58)]:
+            assert rel(W1[a, c].cpu().numpy(), ref[a, c]) < TOL
+        Sref = np.real(np.einsum("abab->ab", ref))
+        assert rel(S1.cpu().numpy(), Sref) < TOL
+        muref = O.degree_of_coherence(ref, *P1)
+        sel = Sref >= 1e-4 * Sref.max()
+        assert rel(mu1.cpu().numpy()[sel], muref[sel]) < TOL
+        del ref
+        ref2 = _oracle(dict(N=N2, z=z2, ff=0, lam=lam2, ap=0.45e-3, lf=0.0, mask=m2, A=1.0))
+        S2ref = np.real(O.spectral_density(ref2))
+        assert rel(S2.cpu().numpy(), S2ref) < TOL
+    pw.pw_batch_destroy(b)
