@@ -174,7 +174,7 @@ __device__ __forceinline__ void fft_stage_stream(const float2* tw, Load load, St
   static_assert(N % R == 0, "radix must divide N");
   constexpr int NJ = N / R;
   constexpr int NB = N * NJ;
-#pragma unroll 1
+#pragma unroll 2
   for (int u = threadIdx.x; u < NB; u += NT) {
     const int line = JFAST ? u / NJ : u % N;
     const int j = JFAST ? u % NJ : u / N;
