@@ -23,12 +23,15 @@ struct GradArgs {
   double c;           // (d/dx)^4
   int farfield;
   double Kq;          // far field: q(xi) = exp(2 pi i Kq n^2) per axis, Kq = d^2/(2 lambda z)
-  double* g3;         // [dL/dsigma_S, dL/dsigma_mu, dL/dA] (accumulated; zeroed by the host)
+  double* part;       // N^2 x 3 per-row partial sums (scratch)
+  double* g3;         // [dL/dsigma_S, dL/dsigma_mu, dL/dA]
   float* gmask;       // N x N dL/da or nullptr
 };
 
 // One CTA per row eta = (ea, eb) of R; R is Hermitian, so the column sums of the mask gradient
 // equal the row sums and dL/da(eta) = 4 Re sum_xi2 conj(W0bar)(eta, xi2) A a(xi2) G(eta, xi2).
+// The row is read as pairs of adjacent elements (16-byte loads, N even), two pairs in flight per
+// thread; the row's three parameter sums go to g.part (reduced by gsm_gradient_reduce).
 __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   extern __shared__ double gsm_sh[];
   const int N = g.N, M = N / 2;
@@ -53,35 +56,35 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   // conj(W0bar)(eta, xi2) = c R q(eta) q*(xi2) in the far field (q of both axes)
   float2 qe = make_float2(1.f, 0.f);
   if (g.farfield) qe = cmul(qx[ea], qx[eb]);
-  const float ae = g.amask ? g.amask[eta] : 1.f;
+  const float* amask = g.amask;
+  const bool ff = g.farfield != 0;
+  const float ae = amask ? amask[eta] : 1.f;
   const float d2 = (float)(d * d);
   const float r2e = (float)((ea - M) * (ea - M) + (M - eb) * (M - eb));  // in units of d^2
   // per-thread partial sums in FP32 (each thread adds N^2 / blockDim terms), reduced in FP64
-  float sS = 0.f, sM = 0.f, sA = 0.f, sa = 0.f;
-  const float2* Rrow = g.R + (size_t)eta * N * N;
-  const int NN = N * N, step = blockDim.x, dc = step / N, de = step - dc * N;
-  int c = threadIdx.x / N, e = threadIdx.x - c * N;
-  for (int x = threadIdx.x; x < NN; x += step) {
-    float2 r = __ldg(Rrow + x);
-    if (g.farfield) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
-    const float t = r.x;  // dW0/dtheta is real: only Re(conj(W0bar)) enters
-    const float G = gx[c] * gy[e];
-    const float ax = g.amask ? __ldg(g.amask + x) : 1.f;
-    const float tG = t * ax * G;
+  float sS = 0.f, sM = 0.f, sA = 0.f;
+  const float4* Rrow = reinterpret_cast<const float4*>(g.R + (size_t)eta * N * N);
+  const int NP = N * N / 2, step = blockDim.x;
+  auto term = [&](float2 r, int c, int e, float ax) {
+    if (ff) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
+    const float tG = r.x * ax * gx[c] * gy[e];  // dW0/dtheta is real: only Re(conj(W0bar)) enters
     const float r2x = (float)((c - M) * (c - M) + (M - e) * (M - e));
     const float dx2 = (float)((ea - c) * (ea - c) + (eb - e) * (eb - e));
     sS = fmaf(tG, r2e + r2x, sS);
     sM = fmaf(tG, dx2, sM);
     sA += tG;
-    e += de;
-    c += dc;
-    if (e >= N) {
-      e -= N;
-      ++c;
-    }
+  };
+#pragma unroll 2
+  for (int p = threadIdx.x; p < NP; p += step) {
+    const float4 rr = __ldg(Rrow + p);
+    const int x = 2 * p, c = x / N, e = x - c * N;  // e even: both elements of the pair in row c
+    float2 am = make_float2(1.f, 1.f);
+    if (amask) am = make_float2(__ldg(amask + x), __ldg(amask + x + 1));  // 4-byte alignment only
+    term(make_float2(rr.x, rr.y), c, e, am.x);
+    term(make_float2(rr.z, rr.w), c, e + 1, am.y);
   }
   // the mask-gradient sum is A * sA; the others scale with w0 = A a(eta) a(xi2) G
-  sa = sA;
+  const float sa = sA;
   sS *= ae * d2;
   sM *= ae * d2;
   sA *= ae;
@@ -96,12 +99,31 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   if (threadIdx.x < 4) {
     double x = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x * 8 + w];
-    const double s3 = g.sigma_S * g.sigma_S * g.sigma_S, m3 = g.sigma_mu * g.sigma_mu * g.sigma_mu;
     // sS, sM carry a(eta) a(xi2) G t (r^2 terms), sA carries a(eta) a(xi2) G t, sa carries a(xi2) G t
-    if (threadIdx.x == 0) atomicAdd(g.g3 + 0, 2.0 * g.c * g.A * x / (2.0 * s3));
-    if (threadIdx.x == 1) atomicAdd(g.g3 + 1, 2.0 * g.c * g.A * x / m3);
-    if (threadIdx.x == 2) atomicAdd(g.g3 + 2, 2.0 * g.c * x);
+    if (threadIdx.x < 3) g.part[(size_t)eta * 3 + threadIdx.x] = x;
     if (threadIdx.x == 3 && g.gmask) g.gmask[eta] = (float)(4.0 * g.c * g.A * x);
+  }
+}
+
+// g3 from the per-row partial sums: one CTA, FP64, a fixed summation order (deterministic).
+__global__ void __launch_bounds__(256) gsm_gradient_reduce(GradArgs g) {
+  __shared__ double red[3][8];
+  const int rows = g.N * g.N;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int r = threadIdx.x; r < rows; r += blockDim.x)
+    for (int k = 0; k < 3; ++k) v[k] += g.part[(size_t)r * 3 + k];
+  for (int k = 0; k < 3; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[threadIdx.x][w];
+    const double s3 = g.sigma_S * g.sigma_S * g.sigma_S, m3 = g.sigma_mu * g.sigma_mu * g.sigma_mu;
+    const double scale = threadIdx.x == 0 ? g.A / s3 : (threadIdx.x == 1 ? 2.0 * g.A / m3 : 2.0);
+    g.g3[threadIdx.x] = g.c * scale * x;
   }
 }
 

@@ -712,12 +712,14 @@ pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double
   g.Kq = d * d / (2.0 * lambda_m * z_m);
   g.g3 = dev_grad3;
   g.gmask = dev_grad_mask;
-  cudaError_t e = cudaMemsetAsync(dev_grad3, 0, 3 * sizeof(double), h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "clearing the gradient");
+  g.part = reinterpret_cast<double*>(h->work);  // the work buffer is scratch between propagations
   const size_t sh = 2 * N * sizeof(float) + 2 * N * sizeof(float2) + 32 * sizeof(double) + 64;
   pw::gsm_gradient_kernel<<<N * N, 256, sh, h->stream>>>(g);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+  pw::gsm_gradient_reduce<<<1, 256, 0, h->stream>>>(g);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
   return PW_OK;
 }
 
