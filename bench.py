@@ -402,6 +402,7 @@ def run_batch(args):
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     b = pw.pw_batch_create(insts, pool, ws.data_ptr(), nb, s.cuda_stream)
     chunk = pw.pw_batch_autotune(b)
+    mode = "persistent launch" if pw.pw_batch_get_mode(b) == pw.PW_BATCH_PERSISTENT else "sequenced launches"
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         pw.pw_batch_run(b)
@@ -460,10 +461,11 @@ def run_batch(args):
             "config": {"workload": CFG["name"], "instances": len(specs), "points_per_step": pts,
                        "Ns": list(CFG["Ns"]), "zs": list(CFG["zs"]), "n_freq": CFG["n_freq"],
                        "outputs": "S and mu per instance", "pool": pool, "chunk": chunk,
-                       "launch": "one persistent launch per step, replayed from a CUDA graph"},
+                       "launch": "autotuned mode: %s, replayed from a CUDA graph" % mode},
             "plain_path": {"value": pts / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                            "what": "the same instances through the single-instance calls, one after another"},
-            "gpu_launches": 4 * args.steps, "clocks": clocks}
+            "gpu_launches": (4 if mode.startswith("persistent") else 2 + 2 * len(specs)) * args.steps,
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

@@ -185,11 +185,16 @@ pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int*
  * spectrum), several distances and uneven grid sizes.  Each instance is one propagation of a
  * GSM source (Sec. 5.4) times an optional aperture, thin lens and mask from its source plane;
  * it yields S (Eq. defS) and mu(P1, .) (Eq. defMu) of its output plane, and the whole propagated
- * CSDA when dev_W is given.  All instances run in one persistent launch that walks a work list
- * of (instance, pass, slice chunk) items: pass-B work of an instance starts after its pass-A work,
- * and the half-transformed CSDAs share a pool of `pool` buffers of the largest N (instance i uses
- * slot i mod pool).  pw_batch_run enqueues only device work (no allocation, no synchronisation),
- * so the caller may capture it in a CUDA graph and replay it. */
+ * CSDA when dev_W is given.  Two execution modes (pw_batch_set_mode, chosen by pw_batch_autotune):
+ *   PW_BATCH_PERSISTENT: all instances in one persistent launch that walks a work list of
+ *     (instance, pass, slice chunk) items; pass-B work of an instance starts after its pass-A
+ *     work (bounded waits, see pw_batch_check);
+ *   PW_BATCH_SEQUENCED: the instances one after the other on the single-instance kernels (each
+ *     fills the GPU), with pass B storing S, the mu numerator and W only when dev_W is given.
+ * The default is SEQUENCED when every instance has N >= 64, else PERSISTENT.  In both modes the
+ * half-transformed CSDAs share a pool of `pool` buffers of the largest N (instance i uses slot
+ * i mod pool).  pw_batch_run enqueues only device work (no allocation, no synchronisation), so
+ * the caller may capture it in a CUDA graph and replay it. */
 typedef struct pw_instance {
   int N;                 /* grid size: 16, 32, 64, 96 or 128 */
   double dxi_m, lambda_m, z_m;
@@ -206,6 +211,8 @@ typedef struct pw_instance {
 
 typedef struct pw_batch pw_batch; /* opaque */
 
+enum { PW_BATCH_PERSISTENT = 0, PW_BATCH_SEQUENCED = 1 };
+
 /* Bytes of device workspace pw_batch_create needs for these instances and this pool depth
  * (tables, work list, counters and `pool` half-transformed buffers of the largest N). */
 size_t pw_batch_workspace_bytes(const pw_instance* inst, int n, int pool);
@@ -216,20 +223,27 @@ size_t pw_batch_workspace_bytes(const pw_instance* inst, int n, int pool);
 pw_status pw_batch_create(pw_batch** out, const pw_instance* inst, int n, int pool, void* dev_workspace,
                           size_t workspace_bytes, void* stream);
 
-/* Enqueue one batched run on the batch's stream: counter reset, FP64 tables of every instance,
- * the persistent launch, mu.  Asynchronous; no allocation; capturable in a CUDA graph. */
+/* Enqueue one batched run on the batch's stream: FP64 tables of every instance, then (persistent
+ * mode) counter reset + the persistent launch or (sequenced mode) two pass launches per
+ * instance, then mu.  Asynchronous; no allocation; capturable in a CUDA graph. */
 pw_status pw_batch_run(pw_batch* b);
 
 /* Synchronise and report PW_ETIMEOUT if a bounded dependency wait of a run gave up since the
  * last check (the affected outputs are invalid); clears the condition. */
 pw_status pw_batch_check(pw_batch* b);
 
-/* Slices per work item (>= 4; default 8).  Rebuilds the work list (synchronises). */
+/* Slices per work item of the persistent launch (>= 4; default 8).  Rebuilds the work list
+ * (synchronises). */
 pw_status pw_batch_set_chunk(pw_batch* b, int chunk);
 pw_status pw_batch_get_chunk(const pw_batch* b, int* chunk);
 
-/* Time the run for each candidate chunk size (4 ... 64) and keep the fastest; returns it in
- * *chunk_out if non-NULL.  Runs the batch several times (synchronises). */
+/* Execution mode: PW_BATCH_PERSISTENT or PW_BATCH_SEQUENCED (PW_EINVAL otherwise). */
+pw_status pw_batch_set_mode(pw_batch* b, int mode);
+pw_status pw_batch_get_mode(const pw_batch* b, int* mode);
+
+/* Time the sequenced run and the persistent run at each candidate chunk size (4 ... 64), keep
+ * the fastest mode and chunk; returns the chunk in *chunk_out if non-NULL.  Runs the batch
+ * several times (synchronises). */
 pw_status pw_batch_autotune(pw_batch* b, int* chunk_out);
 
 /* Failure-detection test hook (no counterpart in the paper): leave the pass-A work of

@@ -71,6 +71,8 @@ for _name, (_res, _args) in {
     "pw_batch_check": (_i, [_vp]),
     "pw_batch_set_chunk": (_i, [_vp, _i]),
     "pw_batch_get_chunk": (_i, [_vp, ctypes.POINTER(_i)]),
+    "pw_batch_set_mode": (_i, [_vp, _i]),
+    "pw_batch_get_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_batch_autotune": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_batch_inject_stall": (_i, [_vp, _i, _d]),
     "pw_batch_destroy": (_i, [_vp]),
@@ -231,6 +233,19 @@ def pw_batch_get_chunk(b):
     c = _i()
     _check(LIB.pw_batch_get_chunk(b, ctypes.byref(c)))
     return c.value
+
+
+PW_BATCH_PERSISTENT, PW_BATCH_SEQUENCED = 0, 1
+
+
+def pw_batch_set_mode(b, mode):
+    _check(LIB.pw_batch_set_mode(b, mode))
+
+
+def pw_batch_get_mode(b):
+    m = ctypes.c_int()
+    _check(LIB.pw_batch_get_mode(b, ctypes.byref(m)))
+    return m.value
 
 
 def pw_batch_autotune(b):

@@ -12,9 +12,11 @@
 #include "../../include/pywolf_gb.h"
 #include "batch.cuh"
 
-namespace pwi {
-void set_last_error(const char* msg);                        // pywolf_gb.cu
-pw_status encode_vmap(CUtensorMap* map, void* work, int N);  // pywolf_gb.cu
+namespace pwi {  // pywolf_gb.cu
+void set_last_error(const char* msg);
+pw_status encode_vmap(CUtensorMap* map, void* work, int N);
+cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                                  const float2* Ein, const float2* mask, int ap_ithr, cudaStream_t s);
 }
 
 namespace {
@@ -93,6 +95,8 @@ Layout layout(const pw_instance* in, int n, int pool) {
 
 struct pw_batch {
   int n, pool, chunk;
+  int mode;  // PW_BATCH_PERSISTENT or PW_BATCH_SEQUENCED
+  std::vector<CUtensorMap> vmaps;  // per instance: its V slot in the layout of its N
   char* base;
   Layout L;
   cudaStream_t stream;
@@ -184,6 +188,19 @@ pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->stalled.assign(n, 0);
   b->wait_cycles = 2000000000LL;  // ~1 s at 2 GHz
+  // sequenced launches fill the GPU with one instance at a time from N = 64 on; smaller instances
+  // are too small for that and share the persistent launch
+  bool all_large = true;
+  for (int i = 0; i < n; ++i) all_large = all_large && in[i].N >= 64;
+  b->mode = all_large ? PW_BATCH_SEQUENCED : PW_BATCH_PERSISTENT;
+  b->vmaps.resize(n);
+  for (int i = 0; i < n; ++i) {
+    pw_status st = pwi::encode_vmap(&b->vmaps[i], b->base + L.pool + L.slot_bytes * (i % pool), in[i].N);
+    if (st != PW_OK) {
+      delete b;
+      return st;
+    }
+  }
   std::vector<pw::TableArgs> targs(n);
   std::vector<float2*> mus(n);
   b->inst.resize(n);
@@ -291,13 +308,44 @@ pw_status pw_batch_run(pw_batch* b) {
   pwi::set_last_error("");
   if (!b) return fail(PW_EINVAL, "null batch");
   int* cnt = reinterpret_cast<int*>(b->base + b->L.counters);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (2 * (size_t)b->n + 1), b->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "resetting the batch counters");
+  cudaError_t e;
+  if (b->mode == PW_BATCH_PERSISTENT) {
+    e = cudaMemsetAsync(cnt, 0, sizeof(int) * (2 * (size_t)b->n + 1), b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting the batch counters");
+  }
   int maxNN = 0;
   for (const auto& d : b->inst) maxNN = d.slices > maxNN ? d.slices : maxNN;
   dim3 tg((maxNN + 255) / 256, b->n);
   pw::batch::batch_tables_kernel<<<tg, 256, 0, b->stream>>>(reinterpret_cast<const pw::TableArgs*>(b->base + b->L.targs));
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch tables launch");
+  if (b->mode == PW_BATCH_SEQUENCED) {
+    // one instance after the other on the single-instance kernels (stream order reuses the slots)
+    for (int i = 0; i < b->n; ++i) {
+      const pw::batch::Inst& d = b->inst[i];
+      pw::PassAArgs a{};
+      a.F = d.F;
+      a.G = d.G;
+      a.tw = d.tw;
+      a.A = d.A;
+      pw::PassBArgs pb{};
+      pb.V = d.V;
+      pb.tw = d.tw;
+      pb.Eout = d.Eout;
+      pb.W = d.W;
+      pb.S = d.S;
+      pb.scale = d.scale;
+      pb.row = d.row;
+      pb.iP = d.iP;
+      pb.jP = d.jP;
+      e = pwi::launch_batch_instance(d.N, b->vmaps[i], a, pb, d.Ein, d.mask, d.ap_ithr, b->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "batch instance launch");
+    }
+    dim3 mg((maxNN + 255) / 256, b->n);
+    pw::batch::batch_mu_kernel<<<mg, 256, 0, b->stream>>>(reinterpret_cast<const pw::batch::Inst*>(b->base + b->L.inst),
+                                                          reinterpret_cast<float2* const*>(b->base + b->L.mu));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch mu launch");
+    return PW_OK;
+  }
   pw::batch::Args g{};
   g.inst = reinterpret_cast<const pw::batch::Inst*>(b->base + b->L.inst);
   g.items = reinterpret_cast<const pw::batch::Item*>(b->base + b->L.items);
@@ -341,6 +389,21 @@ pw_status pw_batch_set_chunk(pw_batch* b, int chunk) {
   return build_items(b);
 }
 
+pw_status pw_batch_set_mode(pw_batch* b, int mode) {
+  pwi::set_last_error("");
+  if (!b) return fail(PW_EINVAL, "null batch");
+  if (mode != PW_BATCH_PERSISTENT && mode != PW_BATCH_SEQUENCED) return fail(PW_EINVAL, "unknown batch mode %d", mode);
+  b->mode = mode;
+  return PW_OK;
+}
+
+pw_status pw_batch_get_mode(const pw_batch* b, int* mode) {
+  pwi::set_last_error("");
+  if (!b || !mode) return fail(PW_EINVAL, "null argument");
+  *mode = b->mode;
+  return PW_OK;
+}
+
 pw_status pw_batch_get_chunk(const pw_batch* b, int* chunk) {
   pwi::set_last_error("");
   if (!b || !chunk) return fail(PW_EINVAL, "null argument");
@@ -351,15 +414,18 @@ pw_status pw_batch_get_chunk(const pw_batch* b, int* chunk) {
 pw_status pw_batch_autotune(pw_batch* b, int* chunk_out) {
   pwi::set_last_error("");
   if (!b) return fail(PW_EINVAL, "null batch");
-  const int cand[] = {4, 8, 16, 32, 64};
+  // candidates: the sequenced launches, and the persistent launch at each chunk size
+  const int cand[][2] = {{PW_BATCH_SEQUENCED, 0},   {PW_BATCH_PERSISTENT, 4},  {PW_BATCH_PERSISTENT, 8},
+                         {PW_BATCH_PERSISTENT, 16}, {PW_BATCH_PERSISTENT, 32}, {PW_BATCH_PERSISTENT, 64}};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "autotune events");
   float best = 1e30f;
-  int best_c = b->chunk;
+  int best_m = b->mode, best_c = b->chunk;
   pw_status st = PW_OK;
-  for (int c : cand) {
-    if ((st = pw_batch_set_chunk(b, c)) != PW_OK) break;
+  for (const auto& mc : cand) {
+    b->mode = mc[0];
+    if (mc[0] == PW_BATCH_PERSISTENT && (st = pw_batch_set_chunk(b, mc[1])) != PW_OK) break;
     if ((st = pw_batch_run(b)) != PW_OK) break;  // warm-up
     cudaEventRecord(e0, b->stream);
     if ((st = pw_batch_run(b)) != PW_OK) break;
@@ -369,13 +435,15 @@ pw_status pw_batch_autotune(pw_batch* b, int* chunk_out) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      best_c = c;
+      best_m = mc[0];
+      best_c = mc[0] == PW_BATCH_PERSISTENT ? mc[1] : best_c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PW_OK) return st;
   if ((st = pw_batch_check(b)) != PW_OK) return st;
+  b->mode = best_m;
   if (chunk_out) *chunk_out = best_c;
   return pw_batch_set_chunk(b, best_c);
 }

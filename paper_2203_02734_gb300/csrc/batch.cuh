@@ -278,9 +278,9 @@ __device__ __noinline__ void item_a_r128(const Inst& in, int first, int count, i
 // Pass-B columns first + k stride (k < count): 8-byte asynchronous gather of the next column
 // while the current one is transformed (each thread refills only the staging slots it alone
 // reads), the inverse-sign 2D DFT in registers, and the epilogue from registers.  The CTAs of
-// the neighbouring items gather the other columns of the same runs at the same time; as in the
-// single-instance pass B, the CTA of column j of a group brings quarter j of the group's block,
-// for its column after next, into L2.
+// the neighbouring items gather the other columns of the same runs at about the same time; each
+// CTA brings the group block of its column after next into L2.
+template <bool STORE_W>
 __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, int stride, float2* smem) {
   using r128::N;
   constexpr int g = vgroup<N>();
@@ -292,7 +292,7 @@ __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, i
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   // the descriptor lives in memory (reference argument): keep its fields in registers
   const float2* V = in.V;
-  float2* W = in.W;
+  float2* W = STORE_W ? in.W : nullptr;
   float* Sd = in.S;
   float2* rw = in.row;
   const float scale = in.scale;
@@ -311,10 +311,14 @@ __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, i
       }
   };
   const int last = first + (count - 1) * stride;
-  auto prefetch = [&](int cdn) {  // quarter cdn mod g of the block of column cdn
+  // the whole g-column block of column cdn: the CTAs of the other columns of the group claim their
+  // items at other times, so the block is not split between them (a second request hits in L2)
+  auto prefetch = [&](int cdn) {
     if (t == 0 && cdn <= last) {
       const int cn = cdn / N, dn = cdn % N;
-      bulk_prefetch_l2(V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
+      const float2* blk = V + (size_t)(cn * (N / g) + dn / g) * g * NN;
+#pragma unroll
+      for (int j = 0; j < g; ++j) bulk_prefetch_l2(blk + (size_t)j * NN, (unsigned)(NN * sizeof(float2)));
     }
   };
   prefetch(first + stride);
@@ -349,7 +353,7 @@ __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, i
           const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
           if (a == c && b == d) Sd[cd] = w.x;
           if (a == iP && b == jP) rw[cd] = w;
-          if (W) W[(size_t)cd * NN + a * N + b] = cconj(w);
+          if (STORE_W) W[(size_t)cd * NN + a * N + b] = cconj(w);
         }
       }
     }
@@ -359,7 +363,8 @@ __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, i
 }
 
 __global__ void __launch_bounds__(NT, 1) batch_kernel(Args g) {
-  extern __shared__ __align__(16) float2 smem[];
+  // 1024-byte alignment: the N = 128 pass-A items leave slices by TMA from the start of this buffer
+  extern __shared__ __align__(1024) float2 smem[];
   __shared__ int s_item, s_ok;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(g.next, 1);
@@ -384,7 +389,10 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(Args g) {
         case 64: run_item<64>(in, it, smem); break;
         case 96: run_item<96>(in, it, smem); break;
         case 128:
-          if (it.pass == 1) item_b_r128(in, it.first, it.count, it.stride, smem);
+          if (it.pass == 1) {
+            if (in.W) item_b_r128<true>(in, it.first, it.count, it.stride, smem);
+            else item_b_r128<false>(in, it.first, it.count, it.stride, smem);
+          }
           else if (in.mask) item_a_r128<true>(in, it.first, it.count, it.stride, smem);
           else item_a_r128<false>(in, it.first, it.count, it.stride, smem);
           break;

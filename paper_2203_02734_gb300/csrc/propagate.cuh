@@ -237,13 +237,20 @@ struct PassBArgs {
   float2* W;
   float* S;
   float scale;
+  float2* row;   // optional: row[x] = W(P1, x) (the mu numerator), P1 = (iP, jP); nullptr = none
+  int iP, jP;
 };
+
+// What pass B stores of the propagated CSDA: nothing (S and the optional row only), the
+// conjugated column as the contiguous row (Hermitian CSDA), or every element at its own place.
+enum WStore { W_NONE = 0, W_HERM = 1, W_GENERAL = 2 };
 
 // Pass B, persistent: CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x + k gridDim.x.
 // Per slice: gather V(., ., c', d') + DFT along a (lanes along b), DFT along b with the
-// epilogue (scale, output propagators, S on the diagonal).  HERM: the conjugated column is the
-// contiguous row W(c', d', ., .), written to shared memory and left by one bulk store.
-template <int N, bool HERM>
+// epilogue (scale, output propagators, S on the diagonal, and with ROW the P1 row).  WST = W_HERM:
+// the conjugated column is the contiguous row W(c', d', ., .), written to shared memory and left
+// by one bulk store; W_GENERAL: strided stores; W_NONE: no store of W.
+template <int N, int WST, bool ROW = false>
 __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
   constexpr int NT = Plan<N>::NT, P = pitch<N>(), S = Plan<N>::stages;
   constexpr size_t NN = (size_t)N * N;
@@ -268,10 +275,13 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
     float* Sd = p.S;
     auto ld0 = [buf](int a, int b) { return buf[a * P + b]; };
-    if constexpr (HERM) {
+    float2* rw = p.row;
+    const int iP = p.iP, jP = p.jP;
+    if constexpr (WST == W_HERM) {
       auto epi = [=](int a, int b, float2 y) {
         const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
         if (a == c && b == d) Sd[cd] = w.x;
+        if (ROW && a == iP && b == jP) rw[cd] = w;
         buf[a * N + b] = cconj(w);
       };
       fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, SyncMid{}, epi);
@@ -286,7 +296,8 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
       auto epi = [=](int a, int b, float2 y) {
         const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
         if (a == c && b == d) Sd[cd] = w.x;
-        W[(size_t)(a * N + b) * NN + cd] = w;
+        if (ROW && a == iP && b == jP) rw[cd] = w;
+        if (WST == W_GENERAL) W[(size_t)(a * N + b) * NN + cd] = w;
       };
       fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, NoMid{}, epi);
     }

@@ -46,6 +46,8 @@ namespace pwi {
 // Sets the thread's message returned by pw_last_error() (used by other translation units).
 void set_last_error(const char* msg) { g_err = msg; }
 pw_status encode_vmap(CUtensorMap* map, void* work, int N);
+cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                                  const float2* Ein, const float2* mask, int ap_ithr, cudaStream_t s);
 }  // namespace pwi
 
 struct pw_csd {
@@ -159,17 +161,19 @@ cudaError_t launch_a_r128(const CUtensorMap& vmap, const pw::PassAArgs& a, const
   return cudaGetLastError();
 }
 
-// N = 128, Hermitian store: register-resident pass B with prefetched gather (r128.cuh).
+// N = 128, Hermitian store or none: register-resident pass B with prefetched gather (r128.cuh).
+template <int WST, bool ROW = false>
 cudaError_t launch_b_r128(const pw::PassBArgs& b, cudaStream_t s) {
   constexpr size_t smem = pw::r128::pass_b_smem();
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_b_r128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(pw::r128::pass_b_r128<WST, ROW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = persistent_grid(pw::r128::pass_b_r128, pw::r128::NT, smem, 128 * 128, &grid);
+    e = persistent_grid(pw::r128::pass_b_r128<WST, ROW>, pw::r128::NT, smem, 128 * 128, &grid);
     if (e != cudaSuccess) return e;
   }
-  pw::r128::pass_b_r128<<<grid, pw::r128::NT, smem, s>>>(b);
+  pw::r128::pass_b_r128<WST, ROW><<<grid, pw::r128::NT, smem, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -214,18 +218,18 @@ cudaError_t launch_b_d256(const pw::PassBArgs& b, cudaStream_t s) {
   return launch_clusters(pw::d256::pass_b_d256, pw::d256::CS, pw::d256::NT, pw::d256::pass_b_smem(), &grid, s, b);
 }
 
-template <int N, bool HERM>
+template <int N, int WST, bool ROW = false>
 cudaError_t launch_b(const pw::PassBArgs& b, cudaStream_t s) {
   constexpr size_t smem = pw::pass_b_smem<N>();
   static int grid = 0;
   if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(pw::pass_b_kernel<N, HERM>,
+    cudaError_t e = cudaFuncSetAttribute(pw::pass_b_kernel<N, WST, ROW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = persistent_grid(pw::pass_b_kernel<N, HERM>, pw::Plan<N>::NT, smem, N * N, &grid);
+    e = persistent_grid(pw::pass_b_kernel<N, WST, ROW>, pw::Plan<N>::NT, smem, N * N, &grid);
     if (e != cudaSuccess) return e;
   }
-  pw::pass_b_kernel<N, HERM><<<grid, pw::Plan<N>::NT, smem, s>>>(b);
+  pw::pass_b_kernel<N, WST, ROW><<<grid, pw::Plan<N>::NT, smem, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -254,11 +258,11 @@ cudaError_t launch_passes(int src, bool herm, const CUtensorMap& vmap, const pw:
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if constexpr (N == 128) {
-    e = herm ? launch_b_r128(b, s) : launch_b<N, false>(b, s);
+    e = herm ? launch_b_r128<pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
   } else if constexpr (N == 256) {
     e = herm ? launch_b_d256(b, s) : cudaErrorNotSupported;
   } else {
-    e = herm ? launch_b<N, true>(b, s) : launch_b<N, false>(b, s);
+    e = herm ? launch_b<N, pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
   }
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
@@ -437,6 +441,29 @@ pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
   return PW_OK;
+}
+
+// One propagation of a batched GSM instance on the single-instance kernels, from the instance's
+// tables: pass A, then pass B with S, the P1 row and, if b.W is set, the Hermitian W store.
+cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                                  const float2* Ein, const float2* mask, int ap_ithr, cudaStream_t s) {
+  R128Extra x{};
+  x.Ein = Ein;
+  x.mask = mask;
+  x.ap_ithr = ap_ithr;
+  cudaError_t e;
+  switch (N) {
+#define PW_BCASE(NN)                                                                                        \
+  case NN:                                                                                                  \
+    if ((e = launch_a_mode<NN, pw::SRC_GSM>(vmap, a, x, s)) != cudaSuccess) return e;                       \
+    if constexpr (NN == 128)                                                                                \
+      return b.W ? launch_b_r128<pw::W_HERM, true>(b, s) : launch_b_r128<pw::W_NONE, true>(b, s);           \
+    else return b.W ? launch_b<NN, pw::W_HERM, true>(b, s) : launch_b<NN, pw::W_NONE, true>(b, s);
+    PW_BCASE(16) PW_BCASE(32) PW_BCASE(64) PW_BCASE(96) PW_BCASE(128)
+#undef PW_BCASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 }  // namespace pwi
 

@@ -316,9 +316,11 @@ constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(f
 // 8-byte asynchronous copies into a staging tile it alone reads: the gather of slice k+1 is in
 // flight while slice k is transformed, and no barrier guards the tile.  The inverse-sign 2D DFT
 // runs in registers (stages_23_half through a 64 KB exchange buffer), and the epilogue (scale,
-// output propagators, S on the diagonal) writes the conjugated column as the contiguous row
-// W(c', d', ., .) straight from registers (Hermitian store).
-static __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
+// output propagators, S on the diagonal, and with ROW the P1 row) writes, for WST = W_HERM, the
+// conjugated column as the contiguous row W(c', d', ., .) straight from registers (Hermitian
+// store); W_NONE stores no W.
+template <int WST, bool ROW = false>
+__global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
   extern __shared__ __align__(1024) float2 smem[];
   float2* stg = smem;
   float2* xb = stg + N * N;
@@ -369,6 +371,8 @@ static __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
     stages_23_half<+1>(v, w3, xb, tw);
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
     float2* Wrow = p.W + (size_t)cd * N * N;
+    float2* rw = p.row;
+    const int iP = p.iP, jP = p.jP;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
 #pragma unroll
@@ -380,7 +384,8 @@ static __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
           const int b = lane + 32 * rq;
           const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
           if (a == c && b == d) p.S[cd] = w.x;
-          Wrow[a * N + b] = cconj(w);
+          if (ROW && a == iP && b == jP) rw[cd] = w;
+          if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
         }
       }
     }

@@ -1,6 +1,7 @@
-"""Batched runs (many instances in one persistent launch) on the GPU: parity with the FP64
-oracle, repeatability, CUDA-graph replay, the autotuner, and the bounded dependency wait
-(a stalled instance yields PW_ETIMEOUT while the others complete)."""
+"""Batched runs on the GPU, in both execution modes (one persistent launch over all instances;
+the instances one after the other on the single-instance kernels): parity with the FP64 oracle,
+repeatability, CUDA-graph replay, the autotuner, and the bounded dependency wait of the
+persistent launch (a stalled instance yields PW_ETIMEOUT while the others complete)."""
 import numpy as np
 import pytest
 
@@ -71,10 +72,12 @@ def _check(bufs, srcs):
     return errs
 
 
-def test_batch_matches_oracle_and_repeats():
+@pytest.mark.parametrize("mode", ["persistent", "sequenced"])
+def test_batch_matches_oracle_and_repeats(mode):
     import torch
     import paper_2203_02734_gb300 as pw
     b, bufs, srcs, ws = _setup(torch, pw)
+    pw.pw_batch_set_mode(b, pw.PW_BATCH_PERSISTENT if mode == "persistent" else pw.PW_BATCH_SEQUENCED)
     pw.pw_batch_run(b)
     pw.pw_batch_check(b)
     _check(bufs, srcs)
@@ -93,6 +96,7 @@ def test_batch_graph_replay_and_autotune():
     b, bufs, srcs, ws = _setup(torch, pw, stream=s)
     chunk = pw.pw_batch_autotune(b)
     assert chunk in (4, 8, 16, 32, 64) and pw.pw_batch_get_chunk(b) == chunk
+    assert pw.pw_batch_get_mode(b) in (pw.PW_BATCH_PERSISTENT, pw.PW_BATCH_SEQUENCED)
     with torch.cuda.stream(s):
         pw.pw_batch_run(b)
     s.synchronize()
@@ -116,6 +120,7 @@ def test_batch_stalled_instance_times_out():
     import paper_2203_02734_gb300 as pw
     # a pool slot per instance: no other instance waits on the stalled one's buffer
     b, bufs, srcs, ws = _setup(torch, pw, pool=len(SPECS))
+    pw.pw_batch_set_mode(b, pw.PW_BATCH_PERSISTENT)  # the bounded waits belong to the persistent launch
     pw.pw_batch_inject_stall(b, 1, 0.2)
     pw.pw_batch_run(b)
     with pytest.raises(pw.PwError, match="PW_ETIMEOUT"):
@@ -134,9 +139,19 @@ def test_batch_rejects_bad_instances():
     ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
         pw.pw_batch_create(inst, 1, ws.data_ptr(), ws.numel())
+    S16 = torch.empty((16, 16), dtype=torch.float32, device="cuda")
+    ok = [pw.pw_instance(16, DXI, LAM, 0.5, 0, 1e-4, 5e-5, 1.0, 0.0, 0.0, None, 0, 0, None, S16.data_ptr(), None)]
+    nb = pw.pw_batch_workspace_bytes(ok, 1)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(ok, 1, ws.data_ptr(), nb)
+    assert pw.pw_batch_get_mode(b) == pw.PW_BATCH_PERSISTENT  # small instances: the default
+    with pytest.raises(pw.PwError, match="PW_EINVAL"):
+        pw.pw_batch_set_mode(b, 7)
+    pw.pw_batch_destroy(b)
 
 
-def test_batch_mixes_register_engine_n128():
+@pytest.mark.parametrize("mode", ["persistent", "sequenced"])
+def test_batch_mixes_register_engine_n128(mode):
     """An N = 128 instance (register-resident engine: TMA-stored slices, gathered columns) in the
     same launch as an N = 64 one, run twice.  The N = 128 GSM source behind a thin lens is
     separable, so the oracle's per-axis quadrature gives its exact propagated CSDA."""
@@ -159,6 +174,8 @@ def test_batch_mixes_register_engine_n128():
     nb = pw.pw_batch_workspace_bytes(insts, 2)
     ws = torch.full((nb,), 0xAB, dtype=torch.uint8, device="cuda")
     b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, torch.cuda.current_stream().cuda_stream)
+    assert pw.pw_batch_get_mode(b) == pw.PW_BATCH_SEQUENCED  # every N >= 64: the default
+    pw.pw_batch_set_mode(b, pw.PW_BATCH_PERSISTENT if mode == "persistent" else pw.PW_BATCH_SEQUENCED)
     for rep in range(2):
         S1.zero_()
         pw.pw_batch_run(b)
