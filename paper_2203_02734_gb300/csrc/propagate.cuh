@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cluster.cuh"
 #include "fft.cuh"
 
 namespace pw {
@@ -262,8 +263,21 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
     tw[i] = p.tw[i];
     eo[i] = p.Eout[i];
   }
+  // The g columns of one (c', d'/g) share one block of V; the CTA of column j brings part j of the
+  // block of its column after next into L2, so that the gathers (8 bytes from every 32-byte run)
+  // hit L2 instead of waiting on DRAM (V is larger than L2 from N = 32 on).
+  constexpr int g = vgroup<N>();
+  auto prefetch = [&](int cdn) {
+    if (N >= 32 && threadIdx.x == 0 && cdn < N * N) {
+      const int cn = cdn / N, dn = cdn % N;
+      bulk_prefetch_l2(p.V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
+    }
+  };
+  prefetch(blockIdx.x);
+  prefetch(blockIdx.x + gridDim.x);
   __syncthreads();
   for (int cd = blockIdx.x; cd < N * N; cd += gridDim.x) {
+    prefetch(cd + 2 * gridDim.x);
     const int c = cd / N, d = cd - c * N;
     const float2* Vg = p.V + v_offset<N>(0, c, d);
     auto gather = [Vg](int b, int a) { return __ldg(Vg + (size_t)(a * N + b) * vgroup<N>()); };
