@@ -156,3 +156,19 @@ def test_invariants_full_size_n128():
     assert abs(out["S"].sum() * dx ** 2 / (S0.sum() * dxi ** 2) - 1) < 1e-5
     assert out["S"].min() > -1e-6 * out["S"].max()
     assert np.abs(out["mu"]).max() <= 1 + 1e-5
+
+
+@pytest.mark.parametrize("kind", ["fresnel", "farfield"])
+def test_output_is_hermitian_non_negative_definite(kind):
+    """A CSD is a Hermitian non-negative definite kernel (Sec. 3.3): the propagated N^2 x N^2 matrix
+    of a random PSD source keeps both properties up to FP32 rounding."""
+    N = 16
+    W0 = WL.random_csd(N, seed=31, n_modes=4)
+    out = gpu_run(N, DXI, LAM, [(kind, 0.35)], array=W0, hermitian=True)
+    M = out["W"].reshape(N * N, N * N)
+    scale = np.abs(M).max()
+    assert np.abs(M - M.conj().T).max() <= 1e-6 * scale
+    ev = np.linalg.eigvalsh(0.5 * (M + M.conj().T))
+    assert ev.min() >= -1e-5 * ev.max()
+    # rank: four modes in, four significant eigenvalues out (propagation is unitary up to scale)
+    assert np.sum(ev > 1e-4 * ev.max()) == 4
