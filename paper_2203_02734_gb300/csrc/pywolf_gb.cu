@@ -16,6 +16,7 @@
 #include "d256.cuh"
 #include "grad.cuh"
 #include "r128.cuh"
+#include "r96.cuh"
 
 namespace {
 
@@ -177,6 +178,37 @@ cudaError_t launch_b_r128(const pw::PassBArgs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// N = 96: register-resident passes (r96.cuh), two CTAs per SM.
+template <int SRC, bool MASK>
+cudaError_t launch_a_r96(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
+  constexpr size_t smem = pw::r96::pass_a_smem();
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(pw::r96::pass_a_r96<SRC, MASK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(pw::r96::pass_a_r96<SRC, MASK>, pw::r96::NT, smem, 96 * 96, &grid);
+    if (e != cudaSuccess) return e;
+  }
+  pw::r96::pass_a_r96<SRC, MASK><<<grid, pw::r96::NT, smem, s>>>(vmap, a, x.Ein, x.mask, x.ap_ithr);
+  return cudaGetLastError();
+}
+
+template <int WST, bool ROW = false>
+cudaError_t launch_b_r96(const pw::PassBArgs& b, cudaStream_t s) {
+  constexpr size_t smem = pw::r96::pass_b_smem();
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(pw::r96::pass_b_r96<WST, ROW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(pw::r96::pass_b_r96<WST, ROW>, pw::r96::NT, smem, 96 * 96, &grid);
+    if (e != cudaSuccess) return e;
+  }
+  pw::r96::pass_b_r96<WST, ROW><<<grid, pw::r96::NT, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
 // Persistent launch of a kernel compiled for clusters of `cs` CTAs: as many clusters as can be
 // co-resident (queried once per kernel).
 template <class K, class... Args>
@@ -239,6 +271,8 @@ template <int N, int SRC>
 cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   if constexpr (N == 128) {
     return x.mask ? launch_a_r128<SRC, true>(vmap, a, x, s) : launch_a_r128<SRC, false>(vmap, a, x, s);
+  } else if constexpr (N == 96) {
+    return x.mask ? launch_a_r96<SRC, true>(vmap, a, x, s) : launch_a_r96<SRC, false>(vmap, a, x, s);
   } else if constexpr (N == 256) {
     return x.mask ? launch_a_d256<SRC, true>(vmap, a, x, s) : launch_a_d256<SRC, false>(vmap, a, x, s);
   } else {
@@ -259,6 +293,8 @@ cudaError_t launch_passes(int src, bool herm, const CUtensorMap& vmap, const pw:
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if constexpr (N == 128) {
     e = herm ? launch_b_r128<pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
+  } else if constexpr (N == 96) {
+    e = herm ? launch_b_r96<pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
   } else if constexpr (N == 256) {
     e = herm ? launch_b_d256(b, s) : cudaErrorNotSupported;
   } else {
@@ -458,6 +494,8 @@ cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::Pass
     if ((e = launch_a_mode<NN, pw::SRC_GSM>(vmap, a, x, s)) != cudaSuccess) return e;                       \
     if constexpr (NN == 128)                                                                                \
       return b.W ? launch_b_r128<pw::W_HERM, true>(b, s) : launch_b_r128<pw::W_NONE, true>(b, s);           \
+    else if constexpr (NN == 96)                                                                            \
+      return b.W ? launch_b_r96<pw::W_HERM, true>(b, s) : launch_b_r96<pw::W_NONE, true>(b, s);             \
     else return b.W ? launch_b<NN, pw::W_HERM, true>(b, s) : launch_b<NN, pw::W_NONE, true>(b, s);
     PW_BCASE(16) PW_BCASE(32) PW_BCASE(64) PW_BCASE(96) PW_BCASE(128)
 #undef PW_BCASE
