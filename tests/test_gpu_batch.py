@@ -167,10 +167,16 @@ def test_batch_mixes_register_engine_n128(mode):
     S2 = torch.empty((N2, N2), dtype=torch.float32, device="cuda")
     mu2 = torch.empty((N2, N2), dtype=torch.complex64, device="cuda")
     P1 = (N1 // 2, N1 // 2 - 3)
+    N3, z3, lam3, lf3 = 96, 0.8, 620e-9, 0.5  # register-resident N = 96 engine, S and mu only
+    S3 = torch.empty((N3, N3), dtype=torch.float32, device="cuda")
+    mu3 = torch.empty((N3, N3), dtype=torch.complex64, device="cuda")
+    P3 = (47, 50)
     insts = [pw.pw_instance(N1, DXI, lam1, z1, 0, 0.1e-3, 0.05e-3, A1, 0.0, lf1, None, P1[0], P1[1],
                             W1.data_ptr(), S1.data_ptr(), mu1.data_ptr()),
              pw.pw_instance(N2, DXI, lam2, z2, 0, 0.1e-3, 0.05e-3, 1.0, 0.45e-3, 0.0, m2t.data_ptr(), 30, 33,
-                            None, S2.data_ptr(), mu2.data_ptr())]
+                            None, S2.data_ptr(), mu2.data_ptr()),
+             pw.pw_instance(N3, DXI, lam3, z3, 0, 0.1e-3, 0.05e-3, 0.9, 0.0, lf3, None, P3[0], P3[1],
+                            None, S3.data_ptr(), mu3.data_ptr())]
     nb = pw.pw_batch_workspace_bytes(insts, 2)
     ws = torch.full((nb,), 0xAB, dtype=torch.uint8, device="cuda")
     b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, torch.cuda.current_stream().cuda_stream)
@@ -193,4 +199,11 @@ def test_batch_mixes_register_engine_n128(mode):
         ref2 = _oracle(dict(N=N2, z=z2, ff=0, lam=lam2, ap=0.45e-3, lf=0.0, mask=m2, A=1.0))
         S2ref = np.real(O.spectral_density(ref2))
         assert rel(S2.cpu().numpy(), S2ref) < TOL
+        ref3 = O.gsm_separable_quadrature(N3, DXI, lam3, z3, 0.1e-3, 0.05e-3, 0.9, lens_f=lf3)
+        S3ref = np.real(np.einsum("abab->ab", ref3))
+        assert rel(S3.cpu().numpy(), S3ref) < TOL
+        mu3ref = O.degree_of_coherence(ref3, *P3)
+        sel = S3ref >= 1e-4 * S3ref.max()
+        assert rel(mu3.cpu().numpy()[sel], mu3ref[sel]) < TOL
+        del ref3
     pw.pw_batch_destroy(b)

@@ -172,3 +172,19 @@ def test_output_is_hermitian_non_negative_definite(kind):
     assert ev.min() >= -1e-5 * ev.max()
     # rank: four modes in, four significant eigenvalues out (propagation is unitary up to scale)
     assert np.sum(ev > 1e-4 * ev.max()) == 4
+
+
+def test_general_array_n96():
+    """Non-Hermitian rank-2 CSDA at N = 96: the register-resident pass A with the general
+    (strided-store) pass B, against the oracle's row probes (Eq. W_fresnel row by row)."""
+    N = 96
+    f = [WL.to_c64((0.5 + 0.5 * WL.uniform01(400 + k, N * N).reshape(N, N))
+                   * np.exp(2j * np.pi * WL.uniform01(500 + k, N * N).reshape(N, N))) for k in range(4)]
+    W0 = (f[0].reshape(-1, 1) * f[1].reshape(1, -1) + f[2].reshape(-1, 1) * f[3].reshape(1, -1))
+    W0 = W0.astype(np.complex64).reshape(N, N, N, N)
+    out = gpu_run(N, DXI, LAM, [("fresnel", 0.45)], array=W0, hermitian=False)
+    rows = [(48, 48), (5, 90), (77, 13)]
+    probe = O.propagate_rows(lambda a, b: W0[a, b].astype(np.complex128), N, DXI, LAM, 0.45, rows)
+    for r, (a, b) in enumerate(rows):
+        assert rel(out["W"][a, b], probe[r]) < TOL
+        assert abs(out["S"][a, b] - probe[r][a, b].real) <= 1e-5 * np.abs(probe[r]).max()
