@@ -24,14 +24,35 @@ struct GradArgs {
   int farfield;
   double Kq;          // far field: q(xi) = exp(2 pi i Kq n^2) per axis, Kq = d^2/(2 lambda z)
   double* part;       // N^2 x 3 per-row partial sums (scratch)
+  float* gtab;        // N x N GSM axis factor G(i, k) (scratch, filled by gsm_gradient_tables)
+  float2* qtab;       // N far-field factors q(x_i) (scratch)
   double* g3;         // [dL/dsigma_S, dL/dsigma_mu, dL/dA]
   float* gmask;       // N x N dL/da or nullptr
 };
 
+// The GSM axis factor G(i, k) = exp(-(x_i^2 + x_k^2)/(4 sigma_S^2) - (x_i - x_k)^2/(2 sigma_mu^2))
+// (the same table serves both axes: y_j = -x_j) and the far-field factors, in FP64, once.
+__global__ void gsm_gradient_tables(GradArgs g) {
+  const int N = g.N, M = N / 2;
+  const double d = g.d;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
+    const int i = idx / N, k = idx - i * N;
+    const double xi = (i - M) * d, xk = (k - M) * d;
+    g.gtab[idx] = (float)exp(-(xi * xi + xk * xk) / (4 * g.sigma_S * g.sigma_S) -
+                             (xi - xk) * (xi - xk) / (2 * g.sigma_mu * g.sigma_mu));
+    if (idx < N) {
+      const double n2 = (double)(idx - M) * (idx - M);
+      g.qtab[idx] = cis_turns(frac_turns(n2 * g.Kq));
+    }
+  }
+}
+
 // One CTA per row eta = (ea, eb) of R; R is Hermitian, so the column sums of the mask gradient
 // equal the row sums and dL/da(eta) = 4 Re sum_xi2 conj(W0bar)(eta, xi2) A a(xi2) G(eta, xi2).
 // The row is read as pairs of adjacent elements (16-byte loads, N even), two pairs in flight per
-// thread; the row's three parameter sums go to g.part (reduced by gsm_gradient_reduce).
+// thread, with the pair's (c, e) advanced incrementally; the row's three parameter sums go to
+// g.part (reduced by gsm_gradient_reduce).  FF: far-field forward propagation.
+template <bool FF>
 __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   extern __shared__ double gsm_sh[];
   const int N = g.N, M = N / 2;
@@ -43,21 +64,15 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   double* red = reinterpret_cast<double*>(qx + 2 * N);
   const double d = g.d;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double xa = (ea - M) * d, xi = (i - M) * d;
-    gx[i] = (float)exp(-(xa * xa + xi * xi) / (4 * g.sigma_S * g.sigma_S) - (xa - xi) * (xa - xi) / (2 * g.sigma_mu * g.sigma_mu));
-    const double yb = (M - eb) * d, yi = (M - i) * d;
-    gy[i] = (float)exp(-(yb * yb + yi * yi) / (4 * g.sigma_S * g.sigma_S) - (yb - yi) * (yb - yi) / (2 * g.sigma_mu * g.sigma_mu));
-    if (g.farfield) {
-      const double n2 = (double)(i - M) * (i - M);
-      qx[i] = cis_turns(frac_turns(n2 * g.Kq));
-    }
+    gx[i] = g.gtab[ea * N + i];  // G along the first axis for row ea
+    gy[i] = g.gtab[eb * N + i];  // G along the second axis for row eb (y_j = -x_j)
+    if (FF) qx[i] = g.qtab[i];
   }
   __syncthreads();
   // conj(W0bar)(eta, xi2) = c R q(eta) q*(xi2) in the far field (q of both axes)
   float2 qe = make_float2(1.f, 0.f);
-  if (g.farfield) qe = cmul(qx[ea], qx[eb]);
+  if (FF) qe = cmul(qx[ea], qx[eb]);
   const float* amask = g.amask;
-  const bool ff = g.farfield != 0;
   const float ae = amask ? amask[eta] : 1.f;
   const float d2 = (float)(d * d);
   const float r2e = (float)((ea - M) * (ea - M) + (M - eb) * (M - eb));  // in units of d^2
@@ -66,7 +81,7 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
   const float4* Rrow = reinterpret_cast<const float4*>(g.R + (size_t)eta * N * N);
   const int NP = N * N / 2, step = blockDim.x;
   auto term = [&](float2 r, int c, int e, float ax) {
-    if (ff) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
+    if (FF) r = cmul(r, cmul(qe, cconj(cmul(qx[c], qx[e]))));
     const float tG = r.x * ax * gx[c] * gy[e];  // dW0/dtheta is real: only Re(conj(W0bar)) enters
     const float r2x = (float)((c - M) * (c - M) + (M - e) * (M - e));
     const float dx2 = (float)((ea - c) * (ea - c) + (eb - e) * (eb - e));
@@ -74,14 +89,23 @@ __global__ void __launch_bounds__(256) gsm_gradient_kernel(GradArgs g) {
     sM = fmaf(tG, dx2, sM);
     sA += tG;
   };
+  // element x = 2 p of the pair: (c, e) = (x / N, x mod N), e even (N even)
+  const int dc = (2 * step) / N, de = (2 * step) - dc * N;
+  int c = (2 * threadIdx.x) / N, e = 2 * threadIdx.x - c * N;
 #pragma unroll 2
   for (int p = threadIdx.x; p < NP; p += step) {
     const float4 rr = __ldg(Rrow + p);
-    const int x = 2 * p, c = x / N, e = x - c * N;  // e even: both elements of the pair in row c
+    const int x = 2 * p;
     float2 am = make_float2(1.f, 1.f);
     if (amask) am = make_float2(__ldg(amask + x), __ldg(amask + x + 1));  // 4-byte alignment only
     term(make_float2(rr.x, rr.y), c, e, am.x);
     term(make_float2(rr.z, rr.w), c, e + 1, am.y);
+    e += de;
+    c += dc;
+    if (e >= N) {
+      e -= N;
+      ++c;
+    }
   }
   // the mask-gradient sum is A * sA; the others scale with w0 = A a(eta) a(xi2) G
   const float sa = sA;

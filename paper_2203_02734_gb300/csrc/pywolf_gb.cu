@@ -777,9 +777,16 @@ pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double
   g.Kq = d * d / (2.0 * lambda_m * z_m);
   g.g3 = dev_grad3;
   g.gmask = dev_grad_mask;
-  g.part = reinterpret_cast<double*>(h->work);  // the work buffer is scratch between propagations
+  // the work buffer is scratch between propagations: partial sums, then the FP64-built tables
+  g.part = reinterpret_cast<double*>(h->work);
+  g.gtab = reinterpret_cast<float*>(g.part + (size_t)N * N * 3);
+  g.qtab = reinterpret_cast<float2*>(g.gtab + (size_t)N * N + (N & 1));
+  pw::gsm_gradient_tables<<<(N * N + 255) / 256, 256, 0, h->stream>>>(g);
+  cudaError_t e0 = cudaGetLastError();
+  if (e0 != cudaSuccess) return cuda_fail(e0, "gradient table launch");
   const size_t sh = 2 * N * sizeof(float) + 2 * N * sizeof(float2) + 32 * sizeof(double) + 64;
-  pw::gsm_gradient_kernel<<<N * N, 256, sh, h->stream>>>(g);
+  if (g.farfield) pw::gsm_gradient_kernel<true><<<N * N, 256, sh, h->stream>>>(g);
+  else pw::gsm_gradient_kernel<false><<<N * N, 256, sh, h->stream>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   pw::gsm_gradient_reduce<<<1, 256, 0, h->stream>>>(g);
