@@ -323,3 +323,29 @@ def test_s_loss_gradient_matches_central_differences(farfield):
         am_[a, b] -= h
         fd = (f(am=ap) - f(am=am_)) / (2 * h)
         assert abs(fd - ga[a, b]) < 1e-6 * np.abs(ga).max()
+
+
+def test_imaging_system_maps_source_onto_image():
+    """Sec. 2.3 imaging system: source plane A, a thin lens f at plane B (R1 from A), image plane C
+    (R2 from B) with the lens law 1/R1 + 1/R2 = 1/f (Eq. imaging).  At unit magnification
+    (R1 = R2 = 2 f) the output sampling equals the source sampling and S_C = C' S_A with C' = 1
+    under the power-conserving scale, on the inverted grid (the two transforms of each point
+    compose to x -> -x; index i -> (N - i) mod N); exact for the discrete method, whatever the
+    input chirp.  At magnification 2 the sampling doubles and the power is conserved."""
+    N, d, lam, f = 32, 20e-6, 633e-9, 0.2
+    m = WL.amplitude_mask(N, seed=5) * (np.arange(N)[:, None] < 20)  # asymmetric: shows an inversion
+    W0 = O.apply_mask(O.gsm_source(N, d, 0.1e-3, 0.05e-3, 1.0), m)
+    SA = np.real(O.spectral_density(W0))
+
+    def image(R1, R2):
+        WB, dB = O.propagate_fft(W0, d, lam, R1)
+        return O.propagate_fft(O.apply_mask(WB, O.thin_lens(N, dB, lam, f)), dB, lam, R2)
+
+    WC, dC = image(2 * f, 2 * f)
+    assert abs(dC / d - 1) < 1e-14
+    rev = (-np.arange(N)) % N
+    SC = np.real(O.spectral_density(WC))
+    assert np.linalg.norm(SC - SA[rev][:, rev]) <= 1e-12 * np.linalg.norm(SA)
+    WC2, dC2 = image(1.5 * f, 3 * f)
+    assert abs(dC2 / d - 2) < 1e-14
+    assert abs(np.real(O.spectral_density(WC2)).sum() * dC2 ** 2 / (SA.sum() * d ** 2) - 1) < 1e-12
