@@ -252,6 +252,15 @@ pw_status pw_batch_autotune(pw_batch* b, int* chunk_out);
  * PW_ETIMEOUT while the other instances complete.  No device fault is involved. */
 pw_status pw_batch_inject_stall(pw_batch* b, int instance, double wait_s);
 
+/* Polychromatic intensity (Sec. 3.5: I(x) = integral of S(x, omega) over frequency; the paper
+ * leaves polychromatic light to future work, Sec. 6): dev_I (N x N float32, device) =
+ * sum_i weights[i] S_i(x) over all instances, with weights[i] (host, n doubles, copied before the
+ * call returns) carrying the spectrum S0(omega_i) and the quadrature weight.  Needs a common
+ * output grid: every instance with the same N and the same output sampling lambda_i z_i /
+ * (N dxi_i) to 1e-9 relative (e.g. z_i = z0 lambda0 / lambda_i); PW_EINVAL otherwise.  Enqueued
+ * on the batch's stream; reads the S of the last pw_batch_run. */
+pw_status pw_batch_spectral_sum(pw_batch* b, const double* weights, float* dev_I);
+
 /* Synchronise the stream and free the host-side state (the workspace belongs to the caller). */
 pw_status pw_batch_destroy(pw_batch* b);
 

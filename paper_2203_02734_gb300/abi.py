@@ -72,6 +72,7 @@ for _name, (_res, _args) in {
     "pw_batch_set_chunk": (_i, [_vp, _i]),
     "pw_batch_get_chunk": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_batch_set_mode": (_i, [_vp, _i]),
+    "pw_batch_spectral_sum": (_i, [_vp, ctypes.POINTER(_d), _vp]),
     "pw_batch_get_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_batch_autotune": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_batch_inject_stall": (_i, [_vp, _i, _d]),
@@ -236,6 +237,11 @@ def pw_batch_get_chunk(b):
 
 
 PW_BATCH_PERSISTENT, PW_BATCH_SEQUENCED = 0, 1
+
+
+def pw_batch_spectral_sum(b, weights, dev_I):
+    w = (_d * len(weights))(*[float(x) for x in weights])
+    _check(LIB.pw_batch_spectral_sum(b, w, dev_I))
 
 
 def pw_batch_set_mode(b, mode):

@@ -44,7 +44,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace layout (offsets from the base, each part 256-byte aligned).
 struct Layout {
-  size_t inst, targs, mu, items, counters, tmaps, tables, pool, total;
+  size_t inst, targs, mu, items, counters, tmaps, wts, tables, pool, total;
   int max_items;
   size_t slot_bytes;
 };
@@ -74,6 +74,8 @@ Layout layout(const pw_instance* in, int n, int pool) {
   off = align256(off + sizeof(int) * (2 * (size_t)n + 2));
   L.tmaps = off;  // one tensor map per pool slot (N = 128 instances store V by TMA)
   off = align256(off + sizeof(CUtensorMap) * pool);
+  L.wts = off;    // per-instance weights of pw_batch_spectral_sum
+  off = align256(off + sizeof(double) * n);
   L.tables = off;
   for (int i = 0; i < n; ++i) {
     const size_t N = in[i].N, NN = N * N;
@@ -102,6 +104,7 @@ struct pw_batch {
   cudaStream_t stream;
   std::vector<pw::batch::Inst> inst;
   std::vector<int> stalled;  // instances whose pass-A items are left out (failure-detection test)
+  std::vector<double> dx_out;  // output sampling of every instance (lambda z / (N dxi))
   int nitems;
   long long wait_cycles;
 };
@@ -249,6 +252,7 @@ pw_status pw_batch_create(pw_batch** out, const pw_instance* in, int n, int pool
     t.Kin = q.farfield ? -base * invf : base * (1.0 / q.z_m - invf);
     const double dx = lz / (N * q.dxi_m);
     t.Kout = dx * dx / (2.0 * lz);
+    b->dx_out.push_back(dx);
     t.gs = q.dxi_m * q.dxi_m / (4.0 * q.sigma_S_m * q.sigma_S_m);
     t.gm = q.dxi_m * q.dxi_m / (2.0 * q.sigma_mu_m * q.sigma_mu_m);
     if (q.aperture_m > 0.0) {
@@ -387,6 +391,27 @@ pw_status pw_batch_set_chunk(pw_batch* b, int chunk) {
   if (chunk < kMinChunk) return fail(PW_EINVAL, "chunk must be >= %d", kMinChunk);
   b->chunk = chunk;
   return build_items(b);
+}
+
+pw_status pw_batch_spectral_sum(pw_batch* b, const double* weights, float* dev_I) {
+  pwi::set_last_error("");
+  if (!b || !weights || !dev_I) return fail(PW_EINVAL, "null argument");
+  const int N = b->inst[0].N;
+  for (int i = 0; i < b->n; ++i) {
+    if (b->inst[i].N != N) return fail(PW_EINVAL, "instance %d: N = %d differs from instance 0 (N = %d)", i, b->inst[i].N, N);
+    if (std::fabs(b->dx_out[i] / b->dx_out[0] - 1.0) > 1e-9)
+      return fail(PW_EINVAL, "instance %d: output sampling %.9g m differs from instance 0 (%.9g m): no common grid",
+                  i, b->dx_out[i], b->dx_out[0]);
+    if (!std::isfinite(weights[i])) return fail(PW_EINVAL, "weight %d is not finite", i);
+  }
+  double* w = reinterpret_cast<double*>(b->base + b->L.wts);
+  cudaError_t e = cudaMemcpyAsync(w, weights, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the weights");
+  const int NN = N * N;
+  pw::batch::batch_sum_kernel<<<(NN + 255) / 256, 256, 0, b->stream>>>(
+      reinterpret_cast<const pw::batch::Inst*>(b->base + b->L.inst), w, b->n, dev_I, NN);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spectral sum launch");
+  return PW_OK;
 }
 
 pw_status pw_batch_set_mode(pw_batch* b, int mode) {

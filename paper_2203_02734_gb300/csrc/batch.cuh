@@ -429,6 +429,15 @@ __global__ void batch_tables_kernel(const TableArgs* targs) {
   }
 }
 
+// I(x) = sum_i w_i S_i(x) over the instances (common grid), accumulated in FP64.
+__global__ void batch_sum_kernel(const Inst* inst, const double* w, int n, float* I, int NN) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < NN; x += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc += w[i] * (double)inst[i].S[x];
+    I[x] = (float)acc;
+  }
+}
+
 // mu(P1, x) = row(x) / sqrt(S(P1) S(x)) for every instance (blockIdx.y = instance).
 __global__ void batch_mu_kernel(const Inst* inst, float2* const* mu_out) {
   const Inst in = inst[blockIdx.y];

@@ -207,3 +207,38 @@ def test_batch_mixes_register_engine_n128(mode):
         assert rel(mu3.cpu().numpy()[sel], mu3ref[sel]) < TOL
         del ref3
     pw.pw_batch_destroy(b)
+
+
+def test_spectral_sum_on_common_grid():
+    """Polychromatic intensity I = sum_i w_i S_i (Sec. 3.5) over wavelengths placed on one output
+    grid (z_i = z0 lambda0 / lambda_i gives the same sampling lambda_i z_i / (N dxi))."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    N, z0, lam0 = 32, 0.5, 600e-9
+    lams = [550e-9, 600e-9, 650e-9, 700e-9]
+    wts = [0.4, 1.0, 0.8, 0.3]
+    Ss = [torch.empty((N, N), dtype=torch.float32, device="cuda") for _ in lams]
+    insts = [pw.pw_instance(N, DXI, lam, z0 * lam0 / lam, 0, 0.1e-3, 0.05e-3, 1.0, 0.25e-3, 0.0, None, 16, 16,
+                            None, S.data_ptr(), None) for lam, S in zip(lams, Ss)]
+    nb = pw.pw_batch_workspace_bytes(insts, 2)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb)
+    I = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    pw.pw_batch_run(b)
+    pw.pw_batch_spectral_sum(b, wts, I.data_ptr())
+    pw.pw_batch_check(b)
+    ref = np.zeros((N, N))
+    for lam, w in zip(lams, wts):
+        W, _ = oracle_run(N, DXI, lam, [("fresnel", z0 * lam0 / lam)], gsm=(0.1e-3, 0.05e-3, 1.0), aperture=0.25e-3)
+        ref += w * np.real(O.spectral_density(W))
+    assert rel(I.cpu().numpy(), ref) < TOL
+    pw.pw_batch_destroy(b)
+    # different output grids: rejected
+    bad = [pw.pw_instance(N, DXI, lam, z0, 0, 0.1e-3, 0.05e-3, 1.0, 0.0, 0.0, None, 16, 16, None, S.data_ptr(), None)
+           for lam, S in zip(lams[:2], Ss[:2])]
+    nb = pw.pw_batch_workspace_bytes(bad, 1)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(bad, 1, ws.data_ptr(), nb)
+    with pytest.raises(pw.PwError, match="no common grid"):
+        pw.pw_batch_spectral_sum(b, [1.0, 1.0], I.data_ptr())
+    pw.pw_batch_destroy(b)
