@@ -134,10 +134,16 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU helpers
-def kernel_source_sha():
-    """Hash of the device-code headers the N = 128 pass kernels are built from."""
+# Per grid size: the committed ncu summary of its pass kernels and the device-code headers they
+# are built from (a recorded traffic figure is used only while those headers are unchanged).
+PROFILED = {128: ("pass_kernels_n128.md", ("cluster.cuh", "fft.cuh", "propagate.cuh", "r128.cuh")),
+            256: ("pass_kernels_n256.md", ("cluster.cuh", "fft.cuh", "propagate.cuh", "d256.cuh"))}
+
+
+def kernel_source_sha(N=128):
+    """Hash of the device-code headers the pass kernels at grid size N are built from."""
     h = hashlib.sha256()
-    for name in ("cluster.cuh", "fft.cuh", "propagate.cuh", "r128.cuh"):
+    for name in PROFILED[N][1]:
         h.update(open(os.path.join(ROOT, "paper_2203_02734_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -150,16 +156,17 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
-    kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "pass_kernels_n128.md")
+def recorded_traffic(kernel, N):
+    """DRAM bytes per launch of `kernel` at grid size N from the committed ncu summary, or None
+    when there is none or the kernel sources changed since it was taken."""
+    if N not in PROFILED:
+        return None
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", PROFILED[N][0])).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch %s (\d+) sha=(\w+)" % kernel, txt)
-    if not m or m.group(2) != kernel_source_sha():
+    if not m or m.group(2) != kernel_source_sha(N):
         return None
     return int(m.group(1))
 
@@ -350,7 +357,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2: 2 x %.1f GB CSDA buffers stream through HBM every step"
                          % (8 * pts / 1e9)},
         "roofline": {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern),
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern, N),
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "pass_ms": {"pass_a": avg_a, "pass_b": avg_b},
                      "step_hbm_frac": (24 * pts / (ms / args.steps / 1e3) / 1e9) / peak},

@@ -1,18 +1,20 @@
 // d256.cuh -- the two passes at N = 256, where one 256 x 256 complex64 slice (512 KB) exceeds
-// what one SM holds: each slice is distributed over a cluster of 4 CTAs, CTA r owning the 64
-// rows [64 r, 64 r + 64) of the slice (128 KB, 32 points per thread in registers).
+// what one SM holds: each slice is distributed over a cluster of CS CTAs (CS = 4 or 8), CTA r
+// owning the RPC = 256 / CS rows [RPC r, RPC r + RPC) of the slice, with NT = 8 RPC threads and 32
+// points per thread in registers (RPC x 256 x 8 bytes of shared memory: 128 KB for CS = 4, one
+// CTA per SM; 64 KB for CS = 8, two CTAs per SM, so that one CTA's waits overlap the other's work).
 //
-// 2D DFT of a slice X(p, q) (p = first index, q = second):
-//   q1: radix 16 along q on the CTA's rows (butterfly jq < 16, inputs q = jq + 16 rq), outputs to
-//       the CTA's slab at [row][sw(16 jq + rq)], sw(q) = q ^ ((q >> 4) & 15);
+// 2D DFT of a slice X(p, q) (p = first index, q = second), HALF = RPC / 2:
+//   q1: radix 16 along q on the CTA's rows (butterfly jq < 16, rows rg + HALF h, inputs
+//       q = jq + 16 rq), outputs to the CTA's slab at [row][sw(16 jq + rq)], sw(q) = q ^ ((q >> 4) & 15);
 //   q2: radix 16 along q (inputs jq + 16 rq, twiddles w256^(rq jq)), natural outputs stored at
 //       [row][q' ^ (row & 15)] for the cross-CTA read;
-//   p1: CTA r takes its 64 columns q' = 64 r + 2 lane + e (e = 0, 1): radix 16 along p with inputs
-//       p = jp + 16 rp read as 16-byte pairs from CTA rp / 4 (distributed shared memory), outputs to
-//       the slab at [16 jp + rp][q' - 64 r];
+//   p1: CTA r takes its RPC columns q' = RPC r + 2 pair + e (e = 0, 1; thread t: jp = t / HALF,
+//       pair = t mod HALF): radix 16 along p with inputs p = jp + 16 rp read as 16-byte pairs from
+//       CTA 16 rp / RPC (distributed shared memory), outputs to the slab at [16 jp + rp][q' - RPC r];
 //   p2: radix 16 along p (inputs jp + 16 rp, twiddles w256^(rp jp)), natural outputs (p', q').
 // Every exchange is bank-conflict free: the XOR swizzles give each half-warp 16 distinct 8-byte
-// bank pairs, the 16-byte pair reads are contiguous per warp.
+// bank pairs, the 16-byte pair reads are contiguous per half-warp.
 #pragma once
 #include "cluster.cuh"
 #include "propagate.cuh"
@@ -21,9 +23,15 @@ namespace pw {
 namespace d256 {
 
 constexpr int N = 256;
-constexpr int CS = 4;      // CTAs per cluster (slice rows per CTA: N / CS = 64)
-constexpr int RPC = N / CS;
-constexpr int NT = 512;
+template <int CS> struct Geo {
+  static constexpr int RPC = N / CS;   // slice rows (and p-stage columns) per CTA
+  static constexpr int NT = 8 * RPC;   // threads per CTA (32 points each)
+  static constexpr int HALF = RPC / 2; // q-stage row groups; p-stage column pairs
+  static constexpr int MINB = CS == 8 ? 2 : 1;  // CTAs per SM
+};
+// The cluster sizes the library launches, measured per pass: pass A gains from two CTAs per SM
+// (one CTA's tile store and barriers overlap the other's DFT), pass B loses by it.
+constexpr int CLUSTER_A = 8, CLUSTER_B = 4;
 
 __device__ __forceinline__ int swq(int q) { return q ^ ((q >> 4) & 15); }
 
@@ -33,20 +41,21 @@ template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int
   return w;
 }
 
-// q2 stage from the slab (in place) and the cross-CTA layout; v holds q1 outputs on entry.
-template <int SIGN>
+// q2 stage from the slab (in place) and the cross-CTA layout; v holds q1 outputs on entry, for the
+// slab rows rg + RS h (RS = threads / 16: the slab's rows of one slice, or of two stacked slices).
+template <int RS, int SIGN>
 __device__ __forceinline__ void q_stage2(float2 (&v)[2][16], float2* slab, const float2* tw) {
   const int t = threadIdx.x, jq = t & 15, rg = t >> 4;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int row = rg + 32 * h;
+    const int row = rg + RS * h;
 #pragma unroll
     for (int r = 0; r < 16; ++r) slab[row * N + swq(16 * jq + r)] = v[h][r];
   }
   __syncthreads();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int row = rg + 32 * h;
+    const int row = rg + RS * h;
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[h][r] = slab[row * N + swq(jq + 16 * r)];
 #pragma unroll
@@ -56,25 +65,26 @@ __device__ __forceinline__ void q_stage2(float2 (&v)[2][16], float2* slab, const
   __syncthreads();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int row = rg + 32 * h;
+    const int row = rg + RS * h;
 #pragma unroll
     for (int r = 0; r < 16; ++r) slab[row * N + ((jq + 16 * r) ^ (row & 15))] = v[h][r];
   }
 }
 
-// p1 + p2: on entry every slab of the cluster holds q2 outputs and a cluster barrier has been
-// passed; on return u[e][r] holds the transform at (p' = jp + 16 r, q' = 64 rank + 2 lane + e),
-// jp = warp.  Leaves the own slab free (after a block barrier) for the caller.
-template <int SIGN>
-__device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const float2* tw,
-                                         const unsigned (&rslab)[CS], unsigned rank) {
-  const int t = threadIdx.x, lane = t & 31, jp = t >> 5;
-  const int p0 = RPC * (int)rank + 2 * lane;  // first of the two columns
+// p1 + p2 of one slice: on entry the slice's slab (RPC x N at `slab`, the same offset in every CTA)
+// of every CTA of the cluster holds q2 outputs and a cluster barrier has been passed; on return
+// u[e][r] holds the transform at (p' = jp + 16 r, q' = RPC rank + 2 pair + e), jp = tl / HALF,
+// pair = tl mod HALF, tl = the thread's index among the slice's 8 RPC threads.  Leaves the own
+// slab free (after a block barrier) for the caller.
+template <int CS, int SIGN>
+__device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const float2* tw, unsigned rank, int tl) {
+  constexpr int RPC = Geo<CS>::RPC, HALF = Geo<CS>::HALF, RG = RPC / 16;
+  const int jp = tl / HALF, pair = tl % HALF;
+  const int p0 = RPC * (int)rank + 2 * pair;  // first of the two columns
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
-    const int row = jp + 16 * (r & 3);  // row of p = jp + 16 r in CTA r / 4; row & 15 == jp
-    const unsigned addr = rslab[r >> 2] + (unsigned)((row * N + (p0 ^ (jp & ~1))) * 8);
-    const float4 pr = ld_cluster4(addr);
+    const int row = jp + 16 * (r % RG);  // row of p = jp + 16 r in CTA 16 r / RPC; row & 15 == jp
+    const float4 pr = ld_cluster4(map_rank(slab + row * N + (p0 ^ (jp & ~1)), r / RG));
     const float2 lo = make_float2(pr.x, pr.y), hi = make_float2(pr.z, pr.w);
     u[0][r] = (jp & 1) ? hi : lo;
     u[1][r] = (jp & 1) ? lo : hi;
@@ -85,11 +95,11 @@ __device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const
   float4* slab4 = reinterpret_cast<float4*>(slab);
 #pragma unroll
   for (int r = 0; r < 16; ++r)
-    slab4[((16 * jp + r) * RPC + 2 * lane) / 2] = make_float4(u[0][r].x, u[0][r].y, u[1][r].x, u[1][r].y);
+    slab4[((16 * jp + r) * RPC + 2 * pair) / 2] = make_float4(u[0][r].x, u[0][r].y, u[1][r].x, u[1][r].y);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
-    const float4 pr = slab4[((jp + 16 * r) * RPC + 2 * lane) / 2];
+    const float4 pr = slab4[((jp + 16 * r) * RPC + 2 * pair) / 2];
     u[0][r] = make_float2(pr.x, pr.y);
     u[1][r] = make_float2(pr.z, pr.w);
   }
@@ -103,15 +113,16 @@ __device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const
 }
 
 // Pass A at N = 256, persistent over clusters: cluster k handles point-1 pairs ab = k,
-// k + #clusters, ...  CTA r builds rows c in [64 r, 64 r + 64) of W1(c, d) (GSM x factors, or
+// k + #clusters, ...  CTA r builds rows c in [RPC r, RPC r + RPC) of W1(c, d) (GSM x factors, or
 // the uploaded W0 x factors), runs the 2D DFT (sign -1) with the rest of the cluster, and leaves
-// its 256 x 64 output tile (all c', d' in [64 r, 64 r + 64)) by one TMA tensor store
-// (box {2g floats, 1, 1, 64/g, 256}) into the V layout.
-template <int SRC, bool MASK>
-__global__ void __launch_bounds__(NT, 1)
+// its 256 x RPC output tile (all c', d' in [RPC r, RPC r + RPC)) by one TMA tensor store
+// (box {2g floats, 1, 1, RPC/g, 256}) into the V layout.
+template <int CS, int SRC, bool MASK>
+__global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     pass_a_d256(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
                 const float2* __restrict__ mask, int ap_ithr) {
   constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
+  constexpr int RPC = Geo<CS>::RPC, NT = Geo<CS>::NT, HALF = Geo<CS>::HALF;
   extern __shared__ __align__(1024) float2 smem[];
   float2* slab = smem;  // RPC x N
   float2* tw = slab + RPC * N;
@@ -125,9 +136,6 @@ __global__ void __launch_bounds__(NT, 1)
     tw[i] = p.tw[i];
     ein[i] = Ein[i];
   }
-  unsigned rslab[CS];
-#pragma unroll
-  for (int q = 0; q < CS; ++q) rslab[q] = map_rank(slab, q);
   auto inside = [&](int i, int j) {
     const int ni = i - N / 2, nj = j - N / 2;
     return ap_ithr < 0 || ni * ni + nj * nj <= ap_ithr;
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(NT, 1)
     float2 v[2][16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int c = RPC * (int)rank + rg + 32 * h;
+      const int c = RPC * (int)rank + rg + HALF * h;
       const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], gA[c])) : cmul(s_ab, ein[c]);
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
@@ -167,14 +175,14 @@ __global__ void __launch_bounds__(NT, 1)
     }
     if (t == 0) bulk_wait_read_all();  // the previous tile has left the slab
     __syncthreads();
-    q_stage2<-1>(v, slab, tw);
+    q_stage2<HALF, -1>(v, slab, tw);
     cluster_sync();
     float2 u[2][16];
-    p_stages<-1>(u, slab, tw, rslab, rank);
+    p_stages<CS, -1>(u, slab, tw, rank, t);
     float4* slab4 = reinterpret_cast<float4*>(slab);
 #pragma unroll
     for (int r = 0; r < 16; ++r)
-      slab4[((t >> 5) + 16 * r) * (RPC / 2) + (t & 31)] = make_float4(u[0][r].x, u[0][r].y, u[1][r].x, u[1][r].y);
+      slab4[(t / HALF + 16 * r) * HALF + t % HALF] = make_float4(u[0][r].x, u[0][r].y, u[1][r].x, u[1][r].y);
     fence_proxy_async_smem();
     __syncthreads();
     if (t == 0) {
@@ -187,16 +195,18 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // Pass B at N = 256, persistent over clusters: cluster k handles point-2 output pairs cd = k,
-// k + #clusters, ...  CTA r gathers rows a in [64 r, 64 r + 64) of the strided column
+// k + #clusters, ...  CTA r gathers rows a in [RPC r, RPC r + RPC) of the strided column
 // V(., ., c', d'), runs the inverse-sign 2D DFT with the rest of the cluster, applies the epilogue
-// (scale, output propagators, S on the diagonal) and writes its 64-column part of the contiguous
+// (scale, output propagators, S on the diagonal) and writes its RPC-column part of the contiguous
 // row W(c', d', ., .) (Hermitian store) straight from registers.
-__global__ void __launch_bounds__(NT, 1) pass_b_d256(PassBArgs p) {
+template <int CS>
+__global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB) pass_b_d256(PassBArgs p) {
+  constexpr int RPC = Geo<CS>::RPC, NT = Geo<CS>::NT, HALF = Geo<CS>::HALF;
   extern __shared__ __align__(1024) float2 smem[];
   float2* slab = smem;
   float2* tw = slab + RPC * N;
   float2* eo = tw + N;
-  const int t = threadIdx.x, jq = t & 15, rg = t >> 4, lane = t & 31, jp = t >> 5;
+  const int t = threadIdx.x, jq = t & 15, rg = t >> 4, pair = t % HALF, jp = t / HALF;
   const unsigned rank = cluster_rank();
   const int cluster = blockIdx.x / CS, nclusters = gridDim.x / CS;
   constexpr int g = vgroup<N>();
@@ -205,9 +215,6 @@ __global__ void __launch_bounds__(NT, 1) pass_b_d256(PassBArgs p) {
     tw[i] = p.tw[i];
     eo[i] = p.Eout[i];
   }
-  unsigned rslab[CS];
-#pragma unroll
-  for (int q = 0; q < CS; ++q) rslab[q] = map_rank(slab, q);
   __syncthreads();
   for (int cd = cluster; cd < N * N; cd += nclusters) {
     const int c = cd / N, d = cd - c * N;
@@ -215,19 +222,19 @@ __global__ void __launch_bounds__(NT, 1) pass_b_d256(PassBArgs p) {
     float2 v[2][16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int a = RPC * (int)rank + rg + 32 * h;
+      const int a = RPC * (int)rank + rg + HALF * h;
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[h][r] = __ldg(Vg + (size_t)(a * N + jq + 16 * r) * g);
       Dft<16, +1>::run(v[h]);
     }
     __syncthreads();  // the previous slice's reads of the slab are done
-    q_stage2<+1>(v, slab, tw);
+    q_stage2<HALF, +1>(v, slab, tw);
     cluster_sync();
     float2 u[2][16];
-    p_stages<+1>(u, slab, tw, rslab, rank);
+    p_stages<CS, +1>(u, slab, tw, rank, t);
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
     float2* Wrow = p.W + (size_t)cd * NN;
-    const int b0 = RPC * (int)rank + 2 * lane;
+    const int b0 = RPC * (int)rank + 2 * pair;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int a = jp + 16 * r;
@@ -244,10 +251,12 @@ __global__ void __launch_bounds__(NT, 1) pass_b_d256(PassBArgs p) {
   cluster_sync();  // no CTA leaves while another may still read its slab
 }
 
-constexpr size_t pass_a_smem() {
-  return (size_t)RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
+template <int CS> constexpr size_t pass_a_smem() {
+  return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
 }
-constexpr size_t pass_b_smem() { return (size_t)RPC * N * sizeof(float2) + 2 * N * sizeof(float2); }
+template <int CS> constexpr size_t pass_b_smem() {
+  return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2);
+}
 
 }  // namespace d256
 }  // namespace pw

@@ -241,13 +241,16 @@ cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* gri
 template <int SRC, bool MASK>
 cudaError_t launch_a_d256(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   static int grid = 0;
-  return launch_clusters(pw::d256::pass_a_d256<SRC, MASK>, pw::d256::CS, pw::d256::NT, pw::d256::pass_a_smem(),
-                         &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr);
+  constexpr int CS = pw::d256::CLUSTER_A;
+  return launch_clusters(pw::d256::pass_a_d256<CS, SRC, MASK>, CS, pw::d256::Geo<CS>::NT,
+                         pw::d256::pass_a_smem<CS>(), &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr);
 }
 
 cudaError_t launch_b_d256(const pw::PassBArgs& b, cudaStream_t s) {
   static int grid = 0;
-  return launch_clusters(pw::d256::pass_b_d256, pw::d256::CS, pw::d256::NT, pw::d256::pass_b_smem(), &grid, s, b);
+  constexpr int CS = pw::d256::CLUSTER_B;
+  return launch_clusters(pw::d256::pass_b_d256<CS>, CS, pw::d256::Geo<CS>::NT, pw::d256::pass_b_smem<CS>(), &grid,
+                         s, b);
 }
 
 template <int N, int WST, bool ROW = false>
@@ -461,7 +464,7 @@ pw_status s_mu(pw_csd* h, int iP, int jP, float* S, pw_c32* mu) {
 namespace pwi {
 // 5D map of a work buffer in the V layout, as 32-bit floats: dims (innermost first)
 // (2g floats of one d' run, b, a, d'/g, c'); box = one whole slice {2g, 1, 1, N/g, N}
-// (N = 256: each CTA of a cluster stores a tile of N / 4 columns, d256.cuh).
+// (N = 256: each CTA of a cluster stores a tile of N / CLUSTER_A columns, d256.cuh).
 pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
   const int g = pw::vgroup_of(N);
   auto enc = encode_tiled();
@@ -469,7 +472,7 @@ pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
   const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
   cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
   cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
-  const int cols = N == 256 ? N / pw::d256::CS : N;
+  const int cols = N == 256 ? N / pw::d256::CLUSTER_A : N;
   cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)N};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, work, dims, strides, box, estr,
