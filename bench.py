@@ -109,6 +109,41 @@ def cpu_baseline(min_s=10.0, max_s=30.0):
                       "propagation(s) incl. source build, S and mu, %.1f s" % (SAMPLE_N, runs, el)}
 
 
+PLAIN_N_MAX = 128  # largest grid the plain FP32 CPU path runs at (N = 128: 2.1 GB per CSDA copy)
+
+
+def cpu_plain_fp32(max_s=30.0):
+    """The plain FP32 CPU path (complex64, scipy.fft on every host core) on the workload's
+    configuration, at the workload's N up to PLAIN_N_MAX (the same configuration at that grid
+    above it).  One untimed propagation at N = 32 first (imports, FFT plans)."""
+    import oracle as O
+    from oracle import plain_fp32 as P
+    N = min(CFG["N"], PLAIN_N_MAX)
+
+    def mask(n):
+        if "corr_px" in CFG:
+            return WL.phase_screen(n, seed=WL.SEED, corr_px=CFG["corr_px"])
+        return O.circle_aperture(n, CFG["dxi"], CFG["aperture"]) * O.thin_lens(n, CFG["dxi"], CFG["lam"],
+                                                                               CFG["lens_f"])
+
+    def step(n):
+        P.propagate_gsm_fp32(n, CFG["dxi"], CFG["lam"], CFG["z"], CFG["sigma_S"], CFG["sigma_mu"], CFG["A"],
+                             mask=mask(n))
+
+    step(32)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        step(N)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el + el / runs > max_s or runs >= 3:
+            break
+    return {"value": runs * N ** 4 / el, "unit": UNIT, "cores": P.host_cores(), "kind": "plain FP32 path",
+            "sample": "complex64 array operations + scipy.fft (Algorithm 2 order) on the host cores, the same "
+                      "configuration at N=%d, %d full propagation(s) incl. source build, S and mu, %.1f s"
+                      % (N, runs, el)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -371,6 +406,7 @@ def run_ours(args):
         dist.destroy_process_group()
     if world == 1:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_plain_fp32"] = cpu_plain_fp32()
     print(json.dumps(line), flush=True)
 
 

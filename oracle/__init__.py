@@ -30,5 +30,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   central finite differences of a real loss.
 * ``gsm_closed_form``                       -- pinned by Mandel-Wolf beam-expansion
   factor Delta(z) and radius of curvature R(z) (independent textbook forms).
+
+``oracle.plain_fp32`` (imported on its own, not re-exported here) is not a reference: it is the
+timed multi-threaded complex64 CPU baseline of the benchmark, checked against this FP64 oracle in
+``tests/test_plain_fp32.py``.
 """
 from .csd import *  # noqa: F401,F403
