@@ -53,6 +53,9 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
                    help="default: the N = 128 workload the metric is quoted on")
+    p.add_argument("--dft", choices=["fp32", "tc_bf16x3"], default="fp32",
+                   help="N = 256 only: the first pass's first radix-16 stage as FP32 codelets (default) or on "
+                        "the tensor cores with split-BF16x3 operands")
     a = p.parse_args()
     global CFG
     CFG = WORKLOADS[a.workload]
@@ -172,7 +175,7 @@ def run_reference(args):
 # Per grid size: the committed ncu summary of its pass kernels and the device-code headers they
 # are built from (a recorded traffic figure is used only while those headers are unchanged).
 PROFILED = {128: ("pass_kernels_n128.md", ("cluster.cuh", "fft.cuh", "propagate.cuh", "r128.cuh")),
-            256: ("pass_kernels_n256.md", ("cluster.cuh", "fft.cuh", "propagate.cuh", "d256.cuh"))}
+            256: ("pass_kernels_n256.md", ("cluster.cuh", "fft.cuh", "propagate.cuh", "d256.cuh", "tc16.cuh"))}
 
 
 def kernel_source_sha(N=128):
@@ -288,6 +291,8 @@ def run_ours(args):
     c = pw.CSD(N, CFG["dxi"], CFG["lam"], W=W, work=work, stream=stream)
     h = c.h
     P1 = CFG["P1"]
+    if args.dft == "tc_bf16x3":
+        pw.pw_csd_set_dft_mode(h, pw.PW_DFT_TC_BF16X3)
 
     screen = "corr_px" in CFG
     mask_dev0 = torch.from_numpy(source_mask_host(N)).cuda() if screen else None
@@ -385,7 +390,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": CFG["name"], "N": N, "points_per_step": pts, "dxi_m": CFG["dxi"],
+        "config": {"workload": CFG["name"], "N": N, "dft_first_stage": args.dft, "points_per_step": pts,
+                   "dxi_m": CFG["dxi"],
                    "lambda_m": CFG["lam"], "z_m": CFG["z"], "aperture_m": CFG.get("aperture"),
                    "lens_f_m": CFG.get("lens_f"), "phase_screen_corr_px": CFG.get("corr_px"), "P1": list(P1),
                    "parallelism": "replicas x%d" % world,

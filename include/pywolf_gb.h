@@ -170,6 +170,22 @@ pw_status pw_spectral_density(pw_csd* h, float* dev_S);
  * complex64, device); mu := 0 where S(P1) S(x) <= 0. */
 pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
 
+/* Arithmetic of the first radix-16 DFT stage of the first pass at N = 256 (all other stages
+ * and grid sizes always run FP32 codelets on the CUDA cores; the DFT itself is Algorithm 2's
+ * direct 2D transform over the point-2 pair).
+ *   PW_DFT_FP32 (default): FP32 complex codelet with FP64-derived twiddles.
+ *   PW_DFT_TC_BF16X3: the stage as a GEMM on the tensor cores (tcgen05, BF16 operands, FP32
+ *     accumulation): each FP32 operand split into three BF16 parts, six partial products kept
+ *     (relative error of the stage ~5e-7).  A comparison mode, not a faster one: the split and the
+ *     tensor-memory round trip cost more than the codelet.
+ * Returns PW_EINVAL for an unknown mode, PW_EUNSUPPORTED for PW_DFT_TC_BF16X3 at N != 256.  A
+ * later propagation of a source other than the Gaussian Schell model (with or without masks)
+ * returns PW_EUNSUPPORTED while the tensor-core mode is set.  A bounded device wait of the
+ * tensor-core stage that gives up is reported by pw_csd_check (PW_ETIMEOUT). */
+enum { PW_DFT_FP32 = 0, PW_DFT_TC_BF16X3 = 1 };
+pw_status pw_csd_set_dft_mode(pw_csd* h, int mode);
+pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode);
+
 /* Per-pass timing (measurement aid, no counterpart in the paper).  pw_csd_enable_timing
  * creates CUDA events for up to max_props propagations (0 disables and frees them); each
  * later propagation records events on the handle's stream around its first pass (source +

@@ -33,6 +33,8 @@ SIGNATURES = {
     "pw_csd_reset": (_i, [_vp, _d]),
     "pw_csd_check": (_i, [_vp]),
     "pw_csd_enable_timing": (_i, [_vp, _i]),
+    "pw_csd_set_dft_mode": (_i, [_vp, _i]),
+    "pw_csd_get_dft_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
     "pw_source_aperture": (_i, [_vp, _d]),
@@ -128,6 +130,19 @@ def pw_csd_check(h):
 
 def pw_csd_reset(h, dxi_m):
     _check(LIB.pw_csd_reset(h, dxi_m))
+
+
+PW_DFT_FP32, PW_DFT_TC_BF16X3 = 0, 1
+
+
+def pw_csd_set_dft_mode(h, mode):
+    _check(LIB.pw_csd_set_dft_mode(h, mode))
+
+
+def pw_csd_get_dft_mode(h):
+    m = _i()
+    _check(LIB.pw_csd_get_dft_mode(h, ctypes.byref(m)))
+    return m.value
 
 
 def pw_csd_enable_timing(h, max_props):

@@ -18,6 +18,7 @@
 #pragma once
 #include "cluster.cuh"
 #include "propagate.cuh"
+#include "tc16.cuh"
 
 namespace pw {
 namespace d256 {
@@ -112,17 +113,28 @@ __device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const
   }
 }
 
+// Byte offset of the tensor-core stage's B operand (after the tables), 128-byte aligned.
+template <int CS> __host__ __device__ constexpr size_t tc_b_offset() {
+  return ((size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float) + 127) / 128 * 128;
+}
+
 // Pass A at N = 256, persistent over clusters: cluster k handles point-1 pairs ab = k,
 // k + #clusters, ...  CTA r builds rows c in [RPC r, RPC r + RPC) of W1(c, d) (GSM x factors, or
 // the uploaded W0 x factors), runs the 2D DFT (sign -1) with the rest of the cluster, and leaves
 // its 256 x RPC output tile (all c', d' in [RPC r, RPC r + RPC)) by one TMA tensor store
 // (box {2g floats, 1, 1, RPC/g, 256}) into the V layout.
-template <int CS, int SRC, bool MASK>
+// TC: the first radix-16 stage (q1) runs on the tensor cores with split-BF16x3 operands
+// (tc16.cuh) instead of the FP32 codelet: per half h of the thread's rows, the 256 vectors
+// (row rg + HALF h, jq) of the CTA go through shared memory (the free slab) as two 128-row tiles,
+// tensor memory holds D (columns 64 h + 32 tile), and thread t reads back its own vector t.
+// A bounded wait that gives up sets *err and leaves the stage's outputs zero.
+template <int CS, int SRC, bool MASK, bool TC = false>
 __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     pass_a_d256(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
-                const float2* __restrict__ mask, int ap_ithr) {
+                const float2* __restrict__ mask, int ap_ithr, int* err) {
   constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
   constexpr int RPC = Geo<CS>::RPC, NT = Geo<CS>::NT, HALF = Geo<CS>::HALF;
+  static_assert(!TC || NT == 256, "the tensor-core stage maps thread t to vector t of two 128-row tiles");
   extern __shared__ __align__(1024) float2 smem[];
   float2* slab = smem;  // RPC x N
   float2* tw = slab + RPC * N;
@@ -135,6 +147,17 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
   for (int i = t; i < N; i += NT) {
     tw[i] = p.tw[i];
     ein[i] = Ein[i];
+  }
+  unsigned char* Bm = reinterpret_cast<unsigned char*>(smem) + tc_b_offset<CS>();
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bm + tc16::B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint32_t phase = 0;
+  bool tc_ok = true;
+  if constexpr (TC) {
+    if (t < 32) tc16::tmem_alloc(tslot, 128);
+    if (t == 0) tc16::mbar_init(mbar);
+    tc16::build_b<-1>(Bm, p.tw, t, NT);
+    tc16::fence_before_sync();
   }
   auto inside = [&](int i, int j) {
     const int ni = i - N / 2, nj = j - N / 2;
@@ -171,10 +194,38 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
         if (DIAG) keep = keep && c == a && d == b;
         v[h][r] = keep ? x : make_float2(0.f, 0.f);
       }
-      Dft<16, -1>::run(v[h]);
+      if (!TC) Dft<16, -1>::run(v[h]);
     }
     if (t == 0) bulk_wait_read_all();  // the previous tile has left the slab
     __syncthreads();
+    if constexpr (TC) {
+      tc16::fence_after_sync();
+      const uint32_t tmem = *tslot;
+      unsigned char* Ast = reinterpret_cast<unsigned char*>(slab);  // 2 tiles x 3 splits = 48 KB
+      const int w = t >> 5;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        tc16::stage_row(Ast, 2, t >> 7, t & 127, v[h]);
+        fence_proxy_async_smem();
+        __syncthreads();
+        tc16::fence_after_sync();
+        if (t == 0 && tc_ok) tc16::issue(tmem, 64 * h, Ast, 2, Bm, mbar);
+        bool ok = tc_ok && tc16::mbar_wait(mbar, phase);
+        phase ^= 1u;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && tc_ok && (t & 31) == 0) atomicExch(err, 1);
+        tc_ok = ok;
+        tc16::fence_after_sync();
+        if (ok) {
+          tc16::load_row(v[h], tmem + ((uint32_t)(32 * (w & 3)) << 16) + 64 * h + 32 * (w >> 2));
+        } else {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) v[h][r] = make_float2(0.f, 0.f);
+        }
+      }
+      tc16::fence_before_sync();
+      // The slab is free again: each thread passed the wait, so the MMAs have read their operands.
+    }
     q_stage2<HALF, -1>(v, slab, tw);
     cluster_sync();
     float2 u[2][16];
@@ -191,7 +242,12 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     }
   }
   if (t == 0) bulk_wait_all();
+  if constexpr (TC) tc16::fence_before_sync();
   cluster_sync();  // no CTA leaves while another may still read its slab
+  if constexpr (TC) {
+    tc16::fence_after_sync();
+    if (t < 32) tc16::tmem_dealloc(*tslot, 128);
+  }
 }
 
 // Pass B at N = 256, persistent over clusters: cluster k handles point-2 output pairs cd = k,
@@ -251,8 +307,9 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB) pass_b_d256(PassBA
   cluster_sync();  // no CTA leaves while another may still read its slab
 }
 
-template <int CS> constexpr size_t pass_a_smem() {
-  return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
+template <int CS, bool TC = false> constexpr size_t pass_a_smem() {
+  return TC ? tc_b_offset<CS>() + tc16::B_BYTES + 16
+            : (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
 }
 template <int CS> constexpr size_t pass_b_smem() {
   return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2);

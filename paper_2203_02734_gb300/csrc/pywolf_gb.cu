@@ -79,6 +79,7 @@ struct pw_csd {
   float* S;       // S of the last propagated plane (pass-B epilogue)
   int* err;       // device flag: a bounded wait in a kernel gave up
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
+  int dft_mode;      // PW_DFT_FP32 or PW_DFT_TC_BF16X3 (N = 256 first pass, first stage)
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
   int timed;
@@ -145,6 +146,7 @@ struct R128Extra {
   const float2* mask;
   int ap_ithr;
   int* err;
+  int dft_tc;  // N = 256: first stage of the first pass on the tensor cores
 };
 
 template <int SRC, bool MASK>
@@ -238,12 +240,12 @@ cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* gri
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int SRC, bool MASK>
+template <int SRC, bool MASK, bool TC = false>
 cudaError_t launch_a_d256(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   static int grid = 0;
   constexpr int CS = pw::d256::CLUSTER_A;
-  return launch_clusters(pw::d256::pass_a_d256<CS, SRC, MASK>, CS, pw::d256::Geo<CS>::NT,
-                         pw::d256::pass_a_smem<CS>(), &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr);
+  return launch_clusters(pw::d256::pass_a_d256<CS, SRC, MASK, TC>, CS, pw::d256::Geo<CS>::NT,
+                         pw::d256::pass_a_smem<CS, TC>(), &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr, x.err);
 }
 
 cudaError_t launch_b_d256(const pw::PassBArgs& b, cudaStream_t s) {
@@ -277,6 +279,12 @@ cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const
   } else if constexpr (N == 96) {
     return x.mask ? launch_a_r96<SRC, true>(vmap, a, x, s) : launch_a_r96<SRC, false>(vmap, a, x, s);
   } else if constexpr (N == 256) {
+    if (x.dft_tc) {
+      if constexpr (SRC == pw::SRC_GSM)
+        return x.mask ? launch_a_d256<SRC, true, true>(vmap, a, x, s) : launch_a_d256<SRC, false, true>(vmap, a, x, s);
+      else
+        return cudaErrorNotSupported;
+    }
     return x.mask ? launch_a_d256<SRC, true>(vmap, a, x, s) : launch_a_d256<SRC, false>(vmap, a, x, s);
   } else {
     return launch_a<N, SRC>(vmap, a, s);
@@ -388,6 +396,8 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (h->N == 256 && !herm)
     return fail(PW_EUNSUPPORTED, "N = 256 needs a Hermitian source (the general strided-store second pass "
                                  "exists for N <= 128 only)");
+  if (h->dft_mode == PW_DFT_TC_BF16X3 && h->kind != SRC_GSM)
+    return fail(PW_EUNSUPPORTED, "the tensor-core first stage is built for Gaussian Schell-model sources only");
   pw_status st = build_tables(h, z, farfield);
   if (st != PW_OK) return st;
   const int src = h->kind == SRC_GSM ? pw::SRC_GSM : (h->kind == SRC_DIAGONAL ? pw::SRC_DIAG : pw::SRC_ARRAY);
@@ -413,6 +423,7 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   x.mask = reinterpret_cast<const float2*>(h->mask);
   x.ap_ithr = -1;
   x.err = h->err;
+  x.dft_tc = h->dft_mode == PW_DFT_TC_BF16X3;
   if (h->aperture > 0.0) {
     const double rp = h->aperture / h->d;
     const double thr = rp * rp;  // the FP64 threshold of the table kernel; r^2 is an integer
@@ -687,6 +698,23 @@ pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int*
   *ms_second = sb;
   *count = h->timed;
   h->timed = 0;
+  return PW_OK;
+}
+
+pw_status pw_csd_set_dft_mode(pw_csd* h, int mode) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (mode != PW_DFT_FP32 && mode != PW_DFT_TC_BF16X3) return fail(PW_EINVAL, "unknown DFT mode %d", mode);
+  if (mode == PW_DFT_TC_BF16X3 && h->N != 256)
+    return fail(PW_EUNSUPPORTED, "the tensor-core stage exists for N = 256 only (N = %d)", h->N);
+  h->dft_mode = mode;
+  return PW_OK;
+}
+
+pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode) {
+  g_err.clear();
+  if (!h || !mode) return fail(PW_EINVAL, "null argument");
+  *mode = h->dft_mode;
   return PW_OK;
 }
 

@@ -1,6 +1,8 @@
-"""N = 256 (the slice is distributed over a 4-CTA cluster): the phase-screen GSM workload
+"""N = 256 (the slice is distributed over a cluster of CTAs): the phase-screen GSM workload
 (N = 256, dxi = 20 um, lambda = 633 nm, z = 0.5 m, unit-modulus screen with 3 px correlation)
-against the oracle's row probes, plus Hermiticity, power and trace conservation (GPU)."""
+against the oracle's row probes, plus Hermiticity, power and trace conservation (GPU); and the
+same workload with the first radix-16 stage on the tensor cores (split-BF16x3), whose FP64
+errors for W, S and mu are printed next to those of the FP32 path."""
 import numpy as np
 import pytest
 
@@ -66,4 +68,76 @@ def test_n256_rejects_general_array():
     with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
         pw.pw_source_array(c.h, c.W.data_ptr(), False)
         pw.pw_propagate_fresnel(c.h, 0.5)
+    c.close()
+
+
+def _sample_points(N, n, seed=7):
+    rng = np.random.default_rng(seed)
+    pts = [(int(a), int(b)) for a, b in rng.integers(N // 2 - 40, N // 2 + 40, size=(n, 2))]
+    return pts
+
+
+def _errors_vs_oracle(mode):
+    """Propagate the phase-screen workload in `mode`; return the FP64 errors of W (three full rows),
+    S and mu(P1, .) (at sampled points, each computed by the oracle one row at a time)."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    cfg = WL.PHASE_SCREEN_N256
+    N, dxi, lam, z = cfg["N"], cfg["dxi"], cfg["lam"], cfg["z"]
+    mask = WL.to_c64(WL.phase_screen(N, seed=WL.SEED, corr_px=cfg["corr_px"]))
+    c = pw.CSD(N, dxi, lam)
+    pw.pw_csd_set_dft_mode(c.h, mode)
+    assert pw.pw_csd_get_dft_mode(c.h) == mode
+    mt = torch.from_numpy(mask).cuda()
+    c.source_gsm(cfg["sigma_S"], cfg["sigma_mu"], cfg["A"])
+    c.source_mask(mt)
+    c.propagate_fresnel(z)
+    P1 = tuple(cfg["P1"])
+    S = c.spectral_density().cpu().numpy().astype(np.float64)
+    mu = c.degree_of_coherence(*P1).cpu().numpy().astype(np.complex128)
+    pw.pw_csd_check(c.h)
+    rows = [P1, (120, 137), (140, 122)]
+    Wrows = [c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows]
+    c.close()
+    pts = _sample_points(N, 24)
+    m = mask.astype(np.complex128)
+    ref = O.propagate_rows_gsm(m, N, dxi, lam, z, cfg["sigma_S"], cfg["sigma_mu"], cfg["A"], rows + pts)
+    err_w = max(np.linalg.norm(Wrows[r] - ref[r]) / np.linalg.norm(ref[r]) for r in range(len(rows)))
+    S_ref = np.array([ref[len(rows) + k][a, b].real for k, (a, b) in enumerate(pts)])
+    S_gpu = np.array([S[a, b] for a, b in pts])
+    err_s = np.abs(S_gpu - S_ref).max() / np.abs(S_ref).max()
+    S_P1 = ref[0][P1].real
+    mu_ref = np.array([ref[0][a, b] / np.sqrt(S_P1 * S_ref[k]) for k, (a, b) in enumerate(pts)])
+    mu_gpu = np.array([mu[a, b] for a, b in pts])
+    err_mu = np.abs(mu_gpu - mu_ref).max()
+    return err_w, err_s, err_mu
+
+
+def test_phase_screen_n256_tensor_core_stage():
+    import paper_2203_02734_gb300 as pw
+    fp32 = _errors_vs_oracle(pw.PW_DFT_FP32)
+    tc = _errors_vs_oracle(pw.PW_DFT_TC_BF16X3)
+    print("\nN=256 phase screen, FP64 errors  W rows (rel L2)  S (rel max)  mu (abs max)\n"
+          "  FP32 codelets              %.3e  %.3e  %.3e\n"
+          "  split-BF16x3 tensor cores  %.3e  %.3e  %.3e" % (fp32 + tc))
+    for e in (fp32, tc):
+        assert e[0] < 1e-5 and e[1] < 1e-5 and e[2] < 1e-5, e
+
+
+def test_dft_mode_arguments():
+    import torch
+    import paper_2203_02734_gb300 as pw
+    c = pw.CSD(256, 20e-6, 633e-9)
+    with pytest.raises(pw.PwError, match="PW_EINVAL"):
+        pw.pw_csd_set_dft_mode(c.h, 7)
+    pw.pw_csd_set_dft_mode(c.h, pw.PW_DFT_TC_BF16X3)
+    d = torch.ones((256, 256), dtype=torch.float32, device="cuda")
+    pw.pw_source_diagonal(c.h, d.data_ptr(), 1.0)
+    with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
+        pw.pw_propagate_fresnel(c.h, 0.5)
+    c.close()
+    c = pw.CSD(64, 20e-6, 633e-9)
+    with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
+        pw.pw_csd_set_dft_mode(c.h, pw.PW_DFT_TC_BF16X3)
+    assert pw.pw_csd_get_dft_mode(c.h) == pw.PW_DFT_FP32
     c.close()
