@@ -113,11 +113,6 @@ __device__ __forceinline__ void p_stages(float2 (&u)[2][16], float2* slab, const
   }
 }
 
-// Byte offset of the tensor-core stage's B operand (after the tables), 128-byte aligned.
-template <int CS> __host__ __device__ constexpr size_t tc_b_offset() {
-  return ((size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float) + 127) / 128 * 128;
-}
-
 // Pass A at N = 256, persistent over clusters: cluster k handles point-1 pairs ab = k,
 // k + #clusters, ...  CTA r builds rows c in [RPC r, RPC r + RPC) of W1(c, d) (GSM x factors, or
 // the uploaded W0 x factors), runs the 2D DFT (sign -1) with the rest of the cluster, and leaves
@@ -125,8 +120,11 @@ template <int CS> __host__ __device__ constexpr size_t tc_b_offset() {
 // (box {2g floats, 1, 1, RPC/g, 256}) into the V layout.
 // TC: the first radix-16 stage (q1) runs on the tensor cores with split-BF16x3 operands
 // (tc16.cuh) instead of the FP32 codelet: per half h of the thread's rows, the 256 vectors
-// (row rg + HALF h, jq) of the CTA go through shared memory (the free slab) as two 128-row tiles,
-// tensor memory holds D (columns 64 h + 32 tile), and thread t reads back its own vector t.
+// (row rg + HALF h, jq) of the CTA go through shared memory as two 128-row tiles, tensor memory
+// holds D (columns 64 h + 32 tile), and thread t reads back its own vector t.  The stage lives in
+// the slab while it is free (A 48 KB, then B 6 KB and the mbarrier, rebuilt every slice), so the
+// kernel needs no more shared memory than the FP32 one: at 6 KB more, the occupancy calculator
+// fits one CTA per SM instead of two (15 clusters of 8 instead of 36, measured).
 // A bounded wait that gives up sets *err and leaves the stage's outputs zero.
 template <int CS, int SRC, bool MASK, bool TC = false>
 __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
@@ -148,16 +146,18 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     tw[i] = p.tw[i];
     ein[i] = Ein[i];
   }
-  unsigned char* Bm = reinterpret_cast<unsigned char*>(smem) + tc_b_offset<CS>();
+  unsigned char* Ast = reinterpret_cast<unsigned char*>(slab);  // A: 2 tiles x 3 splits = 48 KB
+  unsigned char* Bm = Ast + 6 * tc16::A_SPLIT_BYTES;                  // B: 6 KB
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Bm + tc16::B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  uint32_t phase = 0;
+  uint32_t tmem = 0;
   bool tc_ok = true;
   if constexpr (TC) {
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);  // read once, before the slab is used
     if (t < 32) tc16::tmem_alloc(tslot, 128);
-    if (t == 0) tc16::mbar_init(mbar);
-    tc16::build_b<-1>(Bm, p.tw, t, NT);
     tc16::fence_before_sync();
+    __syncthreads();
+    tc16::fence_after_sync();
+    tmem = *tslot;
   }
   auto inside = [&](int i, int j) {
     const int ni = i - N / 2, nj = j - N / 2;
@@ -200,20 +200,27 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     __syncthreads();
     if constexpr (TC) {
       tc16::fence_after_sync();
-      const uint32_t tmem = *tslot;
-      unsigned char* Ast = reinterpret_cast<unsigned char*>(slab);  // 2 tiles x 3 splits = 48 KB
       const int w = t >> 5;
+      tc16::build_b<-1>(Bm, tw, t, NT);
+      if (t == 0) tc16::mbar_init(mbar);  // phase 0 for h = 0, phase 1 for h = 1
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         tc16::stage_row(Ast, 2, t >> 7, t & 127, v[h]);
         fence_proxy_async_smem();
         __syncthreads();
         tc16::fence_after_sync();
-        if (t == 0 && tc_ok) tc16::issue(tmem, 64 * h, Ast, 2, Bm, mbar);
-        bool ok = tc_ok && tc16::mbar_wait(mbar, phase);
-        phase ^= 1u;
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok && tc_ok && (t & 31) == 0) atomicExch(err, 1);
+        // One thread issues and waits; the others sleep at the block barrier that shares its result.
+        int okv = 1;
+        if (t == 0) {
+          okv = tc_ok;
+          if (okv) {
+            tc16::issue<2>(tmem, 64 * h, Ast, Bm, mbar);
+            okv = tc16::mbar_wait(mbar, (uint32_t)h);
+            if (!okv) atomicExch(err, 1);
+          }
+          if (h == 1) tc16::mbar_inval(mbar);  // the slab is reused after this stage
+        }
+        const bool ok = __syncthreads_and(okv) != 0;
         tc_ok = ok;
         tc16::fence_after_sync();
         if (ok) {
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
   cluster_sync();  // no CTA leaves while another may still read its slab
   if constexpr (TC) {
     tc16::fence_after_sync();
-    if (t < 32) tc16::tmem_dealloc(*tslot, 128);
+    if (t < 32) tc16::tmem_dealloc(tmem, 128);
   }
 }
 
@@ -307,10 +314,11 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB) pass_b_d256(PassBA
   cluster_sync();  // no CTA leaves while another may still read its slab
 }
 
-template <int CS, bool TC = false> constexpr size_t pass_a_smem() {
-  return TC ? tc_b_offset<CS>() + tc16::B_BYTES + 16
-            : (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
+template <int CS> constexpr size_t pass_a_smem() {
+  return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float);
 }
+// The tensor-core stage's operands and mbarrier fit in the slab's free tail.
+static_assert(6 * tc16::A_SPLIT_BYTES + tc16::B_BYTES + 16 <= Geo<8>::RPC * N * sizeof(float2), "slab too small");
 template <int CS> constexpr size_t pass_b_smem() {
   return (size_t)Geo<CS>::RPC * N * sizeof(float2) + 2 * N * sizeof(float2);
 }

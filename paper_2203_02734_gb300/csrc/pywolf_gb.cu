@@ -211,10 +211,38 @@ cudaError_t launch_b_r96(const pw::PassBArgs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Number of CTAs of the largest grid of `cs`-CTA clusters of `kernel` that can be co-resident.
+template <class K>
+cudaError_t cluster_capacity(K kernel, int cs, int threads, size_t smem, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(cs * num_sms());
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorInvalidConfiguration;
+  *grid = nclusters * cs;
+  return cudaSuccess;
+}
+
 // Persistent launch of a kernel compiled for clusters of `cs` CTAs: as many clusters as can be
-// co-resident (queried once per kernel).
+// co-resident (queried once per kernel, unless *grid is already set).
 template <class K, class... Args>
 cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* grid, cudaStream_t s, Args... args) {
+  if (*grid == 0) {
+    cudaError_t e = cluster_capacity(kernel, cs, threads, smem, grid);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -226,16 +254,6 @@ cudaError_t launch_clusters(K kernel, int cs, int threads, size_t smem, int* gri
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (*grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int nclusters = 0;
-    cfg.gridDim = dim3(cs * num_sms());
-    e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
-    if (e != cudaSuccess) return e;
-    if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    *grid = nclusters * cs;
-  }
   cfg.gridDim = dim3(*grid);
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
@@ -244,8 +262,20 @@ template <int SRC, bool MASK, bool TC = false>
 cudaError_t launch_a_d256(const CUtensorMap& vmap, const pw::PassAArgs& a, const R128Extra& x, cudaStream_t s) {
   static int grid = 0;
   constexpr int CS = pw::d256::CLUSTER_A;
+  if (TC && grid == 0) {
+    // The occupancy calculator fits one CTA per SM for a kernel that uses tensor memory (15
+    // clusters of 8 instead of 36, measured). This one allocates 128 of an SM's 512 columns and
+    // has the registers, threads and shared memory of its FP32 twin, which caps residency at two
+    // CTAs per SM, so it takes the twin's grid (two per SM co-resident, measured: 53.8 -> 32.3 ms).
+    cudaError_t e = cudaFuncSetAttribute(pw::d256::pass_a_d256<CS, SRC, MASK, TC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pw::d256::pass_a_smem<CS>());
+    if (e != cudaSuccess) return e;
+    e = cluster_capacity(pw::d256::pass_a_d256<CS, SRC, MASK, false>, CS, pw::d256::Geo<CS>::NT,
+                         pw::d256::pass_a_smem<CS>(), &grid);
+    if (e != cudaSuccess) return e;
+  }
   return launch_clusters(pw::d256::pass_a_d256<CS, SRC, MASK, TC>, CS, pw::d256::Geo<CS>::NT,
-                         pw::d256::pass_a_smem<CS, TC>(), &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr, x.err);
+                         pw::d256::pass_a_smem<CS>(), &grid, s, vmap, a, x.Ein, x.mask, x.ap_ithr, x.err);
 }
 
 cudaError_t launch_b_d256(const pw::PassBArgs& b, cudaStream_t s) {

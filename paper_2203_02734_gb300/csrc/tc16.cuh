@@ -64,6 +64,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Before the mbarrier's memory is used for anything else.
+__device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
 // Bounded wait for the completion of phase `parity`; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   uint32_t done = 0;
@@ -127,19 +131,22 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 
 // One thread: the 12 MMAs of each of the ntiles tiles (D of tile T at tensor-memory column
 // dcol + 32 T), then one commit that arrives on mbar when they have completed.
-__device__ __forceinline__ void issue(uint32_t tmem, uint32_t dcol, const unsigned char* A, int ntiles,
-                                      const unsigned char* B, uint64_t* mbar) {
-  const int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
-  for (int T = 0; T < ntiles; ++T) {
+template <int NTILES>
+__device__ __forceinline__ void issue(uint32_t tmem, uint32_t dcol, const unsigned char* A, const unsigned char* B,
+                                      uint64_t* mbar) {
+  constexpr int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
+  // The address field is the low 14 bits (16-byte units): operands at fixed offsets from one base
+  // descriptor differ only by offset / 16 (no carry out of the field for a 256 KB window).
+  const uint64_t a0 = sdesc(smem_u32(A), 2048, 128), b0 = sdesc(smem_u32(B), 512, 128);
+  // Tiles innermost: consecutive MMAs go to independent accumulators.
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
+  for (int q = 0; q < 6; ++q)
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const uint64_t ad = sdesc(smem_u32(A + (ti[q] * ntiles + T) * A_SPLIT_BYTES + 2 * s * 2048), 2048, 128);
-        const uint64_t bd = sdesc(smem_u32(B + tj[q] * B_SPLIT_BYTES + 2 * s * 512), 512, 128);
-        mma(tmem + dcol + 32 * T, ad, bd, (q | s) ? 1u : 0u);
-      }
-  }
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int T = 0; T < NTILES; ++T)
+        mma(tmem + dcol + 32 * T, a0 + (((ti[q] * NTILES + T) * A_SPLIT_BYTES + 2 * s * 2048) >> 4),
+            b0 + ((tj[q] * B_SPLIT_BYTES + 2 * s * 512) >> 4), (q | s) ? 1u : 0u);
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                : "memory");
 }
