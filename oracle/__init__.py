@@ -28,6 +28,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   rank-one (coherent) inputs where |mu| = 1 exactly.
 * ``propagate_adjoint``                     -- pinned by the dot-product test and by
   central finite differences of a real loss.
+* ``propagate_padded``                      -- zero padding with cropped output (Sec. 3.2);
+  pinned by brute-force quadrature at the padded output samples (``propagate_direct`` with
+  ``Nz``) and reduces exactly to ``propagate_fft`` at Nz = N.
+* ``padded_dft_matrix``, ``propagate_rows_gsm_padded`` -- the pruned transform as dense matrices,
+  for large N; pinned by ``propagate_padded`` row by row and by the GSM closed form at the padded
+  output sampling (``gsm_closed_form`` with ``Nz``).
 * ``gsm_closed_form``                       -- pinned by Mandel-Wolf beam-expansion
   factor Delta(z) and radius of curvature R(z) (independent textbook forms).
 

@@ -32,7 +32,8 @@ __all__ = [
     "apply_mask", "centred_dft2", "propagate_fft", "propagate_direct", "propagate_rows",
     "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
     "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
-    "propagate_rows_gsm", "s_loss", "s_loss_gradient",
+    "propagate_rows_gsm", "s_loss", "s_loss_gradient", "propagate_padded", "padded_dft_matrix",
+    "propagate_rows_gsm_padded",
 ]
 
 
@@ -152,15 +153,17 @@ def propagate_fft(W0, dxi, lam, z, farfield=False):
     return W6, dx
 
 
-def _kernel_matrix(N, dxi, lam, z, farfield):
+def _kernel_matrix(N, dxi, lam, z, farfield, Nz=None):
     """h(X, xi) on flattened 2D point lists (row: output point X, column: source point xi).
 
     Fresnel: h = exp(i pi |X - xi|^2 / (lambda z)), i.e. Eq. h_free with r expanded to
     second order and Lambda/r -> Lambda/R (Eq. approx_L); the constant exp(ikz) and
     |Lambda|/z are moved into the scale s (they cancel in h* W h up to |Lambda|^2/z^2).
-    Far field: q(xi) -> 1, so h = q(X) exp(-2 pi i X.xi / (lambda z))   (Eq. W_farfield)."""
+    Far field: q(xi) -> 1, so h = q(X) exp(-2 pi i X.xi / (lambda z))   (Eq. W_farfield).
+    Nz: the output grid is the central N x N of the grid of a transform of size Nz (zero padding,
+    Sec. 3.2), spacing lambda z / (Nz dxi)."""
     x, y = axis_coords(N, dxi)
-    dx = output_sampling(N, dxi, lam, z)
+    dx = output_sampling(Nz or N, dxi, lam, z)
     X, Y = axis_coords(N, dx)
     sx = np.stack(np.meshgrid(x, y, indexing="ij"), -1).reshape(-1, 2)
     ox = np.stack(np.meshgrid(X, Y, indexing="ij"), -1).reshape(-1, 2)
@@ -172,18 +175,19 @@ def _kernel_matrix(N, dxi, lam, z, farfield):
     return np.exp(1j * np.pi * d2 / (lam * z))
 
 
-def propagate_direct(W0, dxi, lam, z, farfield=False):
+def propagate_direct(W0, dxi, lam, z, farfield=False, Nz=None):
     """Brute-force quadrature of Eq. W_general on the grid, O(N^8) terms:
 
     W_B(X1, X2) = s * sum_{xi1, xi2} h*(X1, xi1) W0(xi1, xi2) h(X2, xi2),
 
     evaluated as conj(H) @ W0 @ H^T over flattened point indices (two matmuls).
-    Independent of the chirp/DFT factorisation used by propagate_fft.  Small N only."""
+    Independent of the chirp/DFT factorisation used by propagate_fft.  Small N only.
+    Nz: output samples of a zero-padded transform of size Nz (see _kernel_matrix)."""
     N = W0.shape[0]
-    H = _kernel_matrix(N, dxi, lam, z, farfield)
+    H = _kernel_matrix(N, dxi, lam, z, farfield, Nz)
     Wf = np.asarray(W0, dtype=np.complex128).reshape(N * N, N * N)
     WB = propagation_scale(dxi, lam, z) * (np.conj(H) @ Wf @ H.T)
-    return WB.reshape(N, N, N, N), output_sampling(N, dxi, lam, z)
+    return WB.reshape(N, N, N, N), output_sampling(Nz or N, dxi, lam, z)
 
 
 def propagate_rows(source_slice, N, dxi, lam, z, rows, farfield=False):
@@ -266,6 +270,61 @@ def propagate_rows_gsm(m, N, dxi, lam, z, sigma_S, sigma_mu, A, rows, farfield=F
     return out
 
 
+def _check_padding(N, Nz):
+    if Nz < N or (Nz - N) % 2:
+        raise ValueError("the padded size Nz must be >= N with Nz - N even (the source sits at the centre)")
+
+
+def propagate_padded(W0, dxi, lam, z, Nz, farfield=False):
+    """Zero padding with cropped output (Sec. 3.2, the note after Eq. spatial_resolution): the
+    FFT runs on a grid of size Nz > N, N_z takes the place of N in dx = lambda z / (Nz dxi), and
+    the result is cropped back to N x N.  Written out: W0 is placed at the centre of an Nz^4
+    array of zeros (source coordinates unchanged, xi(n) = (n - N/2) dxi), propagated by
+    Algorithm 2 at size Nz (propagate_fft), and the central N^4 block is returned with dx.
+    Small N only (the padded array has Nz^4 elements)."""
+    N = W0.shape[0]
+    _check_even(N)
+    _check_padding(N, Nz)
+    o = (Nz - N) // 2
+    Wp = np.zeros((Nz,) * 4, dtype=np.complex128)
+    Wp[o:o + N, o:o + N, o:o + N, o:o + N] = W0
+    WB, dx = propagate_fft(Wp, dxi, lam, z, farfield)
+    return WB[o:o + N, o:o + N, o:o + N, o:o + N].copy(), dx
+
+
+def padded_dft_matrix(N, Nz, sign):
+    """E[k, n] = exp(sign 2 pi i (k - N/2)(n - N/2) / Nz): the centred DFT of size Nz restricted
+    to its central N inputs (the source; the rest are the padding zeros) and its central N
+    outputs (the crop) -- the pruned transform of propagate_padded along one axis."""
+    k = np.arange(N, dtype=np.float64) - N / 2
+    return np.exp(sign * 2j * np.pi * np.outer(k, k) / Nz)
+
+
+def propagate_rows_gsm_padded(m, N, dxi, lam, z, sigma_S, sigma_mu, A, rows, Nz, farfield=False):
+    """Rows W_B(X1 = (i1', j1'), .) of propagate_padded for the masked GSM source of
+    propagate_rows_gsm, for large N: the point-1 sum as in propagate_rows_gsm (exponential
+    weights at the padded output sampling), the point-2 sum as E inner E^T with the pruned matrix
+    E = padded_dft_matrix(N, Nz, -1) instead of a size-N DFT.  O(N^3) per row."""
+    _check_padding(N, Nz)
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(Nz, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    m = np.asarray(m, dtype=np.complex128)
+    g = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * sigma_S ** 2)
+               - (x[:, None] - x[None, :]) ** 2 / (2 * sigma_mu ** 2))
+    qin = np.ones((N, N), dtype=np.complex128) if farfield else q(z, _r2_grid(N, dxi), lam)
+    qout = q(z, _r2_grid(N, dx), lam)
+    E = padded_dft_matrix(N, Nz, -1)
+    out = np.empty((len(rows), N, N), dtype=np.complex128)
+    for r, (a, b) in enumerate(rows):
+        ph = (X[a] * x[:, None] + Y[b] * y[None, :]) / (lam * z)
+        w = np.conj(qin) * np.exp(2j * np.pi * ph)
+        inner = A * m * (g.T @ (w * np.conj(m)) @ g) * qin
+        out[r] = E @ inner @ E.T
+        out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
+    return out
+
+
 def propagate_adjoint(Y, dxi, lam, z, farfield=False):
     """Adjoint P^H of the linear map P: W0 -> W_B of propagate_fft (Hilbert-Schmidt inner
     product <A, B> = sum conj(A) B).  P = s * D_out . F . D_in with diagonal chirp factors
@@ -310,7 +369,7 @@ def _gsm_axis_gaussian(sigma_S, sigma_mu):
     return a, g
 
 
-def gsm_closed_form(N, dxi, lam, z, sigma_S, sigma_mu, A=1.0, farfield=False):
+def gsm_closed_form(N, dxi, lam, z, sigma_S, sigma_mu, A=1.0, farfield=False, Nz=None):
     """Continuous-integral GSM propagation on the output grid.  The printed Eq. Wbeam of
     Sec. 5.4 is garbled (alpha undefined), so the same integral is restated (reading R8).
 
@@ -318,8 +377,9 @@ def gsm_closed_form(N, dxi, lam, z, sigma_S, sigma_mu, A=1.0, farfield=False):
     exp(-J^T M^-1 J / 2), M = [[a, -g], [-g, a]] + diag(2 pi i/(lambda z), -2 pi i/(lambda z))
     (no diagonal term for far field), a = 1/(2 sigma_S^2) + 1/sigma_mu^2, g = 1/sigma_mu^2,
     J = (2 pi X1/(lambda z), -2 pi X2/(lambda z)).  Each axis carries 1/(lambda z) and the
-    output propagators q*(X1) q(X2); the 4D result is A * Wx[i1', i2'] * Wy[j1', j2']."""
-    dx = output_sampling(N, dxi, lam, z)
+    output propagators q*(X1) q(X2); the 4D result is A * Wx[i1', i2'] * Wy[j1', j2'].
+    Nz: evaluated on the central N x N samples of the output grid of a transform of size Nz."""
+    dx = output_sampling(Nz or N, dxi, lam, z)
     X, Yc = axis_coords(N, dx)
     a, g = _gsm_axis_gaussian(sigma_S, sigma_mu)
     beta = 0.0 if farfield else 2.0 * np.pi / (lam * z)

@@ -349,3 +349,57 @@ def test_imaging_system_maps_source_onto_image():
     WC2, dC2 = image(1.5 * f, 3 * f)
     assert abs(dC2 / d - 2) < 1e-14
     assert abs(np.real(O.spectral_density(WC2)).sum() * dC2 ** 2 / (SA.sum() * d ** 2) - 1) < 1e-12
+
+
+# ---------------------------------------------------------------- zero padding (Sec. 3.2)
+def _lens_aperture_gsm(N, dxi=DXI):
+    m = O.circle_aperture(N, dxi, 2.2 * dxi) * O.thin_lens(N, dxi, LAM, 0.3)
+    return O.apply_mask(O.gsm_source(N, dxi, 0.1e-3, 0.05e-3), m)
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_padded_route_equals_direct_quadrature(farfield):
+    # brute force at the padded output samples (dx = lambda z / (Nz dxi), central N of Nz)
+    W0 = _lens_aperture_gsm(6)
+    a, dxa = O.propagate_padded(W0, DXI, LAM, 0.5, 10, farfield)
+    b, dxb = O.propagate_direct(W0, DXI, LAM, 0.5, farfield, Nz=10)
+    assert dxa == dxb == pytest.approx(LAM * 0.5 / (10 * DXI), rel=1e-15)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-12
+
+
+def test_padded_route_without_padding_is_algorithm2():
+    W0 = _lens_aperture_gsm(8)
+    a, _ = O.propagate_padded(W0, DXI, LAM, 0.5, 8)
+    b, _ = O.propagate_fft(W0, DXI, LAM, 0.5)
+    assert np.array_equal(a, b)
+
+
+def test_padded_rows_match_padded_route():
+    rng = np.random.default_rng(3)
+    N, Nz = 12, 20
+    m = np.exp(2j * np.pi * rng.random((N, N)))
+    W0 = O.apply_mask(O.gsm_source(N, DXI, 0.1e-3, 0.05e-3), m)
+    a, _ = O.propagate_padded(W0, DXI, LAM, 0.5, Nz)
+    rows = [(6, 6), (3, 9), (11, 0)]
+    r = O.propagate_rows_gsm_padded(m, N, DXI, LAM, 0.5, 0.1e-3, 0.05e-3, 1.0, rows, Nz)
+    for k, (i, j) in enumerate(rows):
+        assert np.linalg.norm(r[k] - a[i, j]) / np.linalg.norm(a[i, j]) < 1e-12
+
+
+@pytest.mark.parametrize("Nz,farfield", [(128, False), (160, True)])
+def test_padded_gsm_matches_closed_form(Nz, farfield):
+    # the continuous Gaussian integral on the finer output grid of the padded transform
+    N = 64
+    rows = [(32, 32), (20, 40)]
+    r = O.propagate_rows_gsm_padded(np.ones((N, N)), N, DXI, LAM, 0.5, 0.1e-3, 0.05e-3, 1.0, rows, Nz,
+                                    farfield=farfield)
+    cf = O.gsm_closed_form(N, DXI, LAM, 0.5, 0.1e-3, 0.05e-3, 1.0, farfield=farfield, Nz=Nz)
+    for k, (i, j) in enumerate(rows):
+        assert np.linalg.norm(r[k] - cf[i, j]) / np.linalg.norm(cf[i, j]) < 1e-8
+
+
+def test_padded_rejects_bad_sizes():
+    W0 = _lens_aperture_gsm(6)
+    for Nz in (4, 9):
+        with pytest.raises(ValueError):
+            O.propagate_padded(W0, DXI, LAM, 0.5, Nz)
