@@ -62,14 +62,16 @@ const char* pw_last_error(void);
 /* Name of a status code ("PW_OK", ...). */
 const char* pw_status_string(pw_status s);
 
-/* 1 if this build has a propagation plan for grid size N, else 0. */
+/* 1 if this build has an FFT propagation plan for grid size N, else 0.  Other even N up to
+ * PW_MAX_N propagate on the dense path (see pw_csd_set_padding). */
 int pw_supported_n(int N);
+enum { PW_MAX_N = 512 };
 
 /* Bytes required for each of dev_W and dev_work: N^4 * sizeof(pw_c32). */
 size_t pw_csda_bytes(int N);
 
 /* Create a handle for an N x N x N x N CSDA on the current CUDA device.
- *   N         even, >= 2, with pw_supported_n(N) == 1
+ *   N         even, 2 <= N <= PW_MAX_N (FFT plans where pw_supported_n(N), else the dense path)
  *   dxi_m     sampling d of the source plane in metres (finite, > 0)           (Eq. point)
  *   lambda_m  wavelength in metres (finite, > 0); omega = 2 pi c / lambda     (Eq. q_factor)
  *   dev_W     device buffer of >= pw_csda_bytes(N) bytes: holds an uploaded source CSDA
@@ -169,6 +171,23 @@ pw_status pw_spectral_density(pw_csd* h, float* dev_S);
  * (Eq. defMu, Algorithm coherence) for P1 = (iP, jP), 0 <= iP, jP < N, into dev_mu (N x N
  * complex64, device); mu := 0 where S(P1) S(x) <= 0. */
 pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
+
+/* Zero padding with cropped output (Sec. 3.2: "if we use zero padding to perform the FFT, we must
+ * consider the total size N_z in the term N ... even if we crop the matrix to its original size"):
+ * later propagations evaluate the transform of size Nz of the source placed at the centre of an
+ * Nz x Nz grid, at the central N x N output samples, with output sampling
+ * dx = lambda z / (Nz dxi) instead of lambda z / (N dxi).
+ *   Nz = 0 or Nz = N: no padding (the default).
+ *   Nz > N with Nz - N even: padding.
+ * A padded propagation (and any propagation at an N without an FFT plan) runs as four dense axis
+ * contractions in FP32: the pruned DFT of size Nz with the propagators folded in, one N x N
+ * complex matrix per axis (O(N) work per point instead of O(log N)).  It accepts every source
+ * (GSM, uploaded CSDA, diagonal, propagated plane, with masks), produces the same outputs
+ * (W, S, mu) and ignores pw_csd_set_dft_mode.
+ * Returns PW_EINVAL for Nz < N (other than 0), odd Nz - N or Nz > 1 << 20; kept across
+ * pw_csd_reset. */
+pw_status pw_csd_set_padding(pw_csd* h, int Nz);
+pw_status pw_csd_get_padding(const pw_csd* h, int* Nz);
 
 /* Arithmetic of the first radix-16 DFT stage of the first pass at N = 256 (all other stages
  * and grid sizes always run FP32 codelets on the CUDA cores; the DFT itself is Algorithm 2's

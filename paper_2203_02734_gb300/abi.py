@@ -34,6 +34,8 @@ SIGNATURES = {
     "pw_csd_check": (_i, [_vp]),
     "pw_csd_enable_timing": (_i, [_vp, _i]),
     "pw_csd_set_dft_mode": (_i, [_vp, _i]),
+    "pw_csd_set_padding": (_i, [_vp, _i]),
+    "pw_csd_get_padding": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_get_dft_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
@@ -133,6 +135,17 @@ def pw_csd_reset(h, dxi_m):
 
 
 PW_DFT_FP32, PW_DFT_TC_BF16X3 = 0, 1
+PW_MAX_N = 512
+
+
+def pw_csd_set_padding(h, Nz):
+    _check(LIB.pw_csd_set_padding(h, Nz))
+
+
+def pw_csd_get_padding(h):
+    n = _i()
+    _check(LIB.pw_csd_get_padding(h, ctypes.byref(n)))
+    return n.value
 
 
 def pw_csd_set_dft_mode(h, mode):

@@ -14,6 +14,7 @@
 #include "../../include/pywolf_gb.h"
 #include "propagate.cuh"
 #include "d256.cuh"
+#include "dense.cuh"
 #include "grad.cuh"
 #include "r128.cuh"
 #include "r96.cuh"
@@ -80,6 +81,7 @@ struct pw_csd {
   int* err;       // device flag: a bounded wait in a kernel gave up
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
   int dft_mode;      // PW_DFT_FP32 or PW_DFT_TC_BF16X3 (N = 256 first pass, first stage)
+  int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
   int timed;
@@ -418,11 +420,78 @@ pw_status build_tables(pw_csd* h, double z, bool farfield) {
 
 bool has_masks(const pw_csd* h) { return h->aperture > 0.0 || h->lens_f != 0.0 || h->mask != nullptr; }
 
+// Zero padding (Nz > N) or a grid size without an FFT plan: four dense axis contractions
+// (dense.cuh).  W0 is built in W, then d (W -> work), c (work -> W), b (W -> work) and
+// a (work -> W, with the scale and S).  Events as for the FFT passes: the first two
+// contractions count as the first pass.
+pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
+  const int N = h->N, Nz = h->Nz > 0 ? h->Nz : N;
+  pw_status st = build_tables(h, z, farfield);  // G and M0 (the FFT factors are not used here)
+  if (st != PW_OK) return st;
+  const double d = h->d, lz = h->lambda * z, dx = lz / (Nz * d);
+  cudaEvent_t* ev = nullptr;
+  if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
+  cudaError_t e = cudaSuccess;
+  if (ev && (e = cudaEventRecord(ev[0], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  pw::dense::TabArgs t{};
+  t.N = N;
+  t.Nz = Nz;
+  t.Kin = farfield ? 0.0 : d * d / (2.0 * lz);
+  t.Kout = dx * dx / (2.0 * lz);
+  t.E = h->F;  // the FFT input factor's storage (N x N complex) holds E on this path
+  const int NN = N * N;
+  pw::dense::tables_kernel<<<(NN + 255) / 256, 256, 0, h->stream>>>(t);
+  pw::dense::SrcArgs sa{};
+  sa.N = N;
+  sa.mode = h->kind == SRC_GSM ? pw::SRC_GSM : (h->kind == SRC_DIAGONAL ? pw::SRC_DIAG : pw::SRC_ARRAY);
+  sa.G = h->G;
+  sa.M0 = h->M0;
+  sa.W0 = reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0);
+  sa.diag = h->diag;
+  sa.A = (float)h->A;
+  sa.W = reinterpret_cast<float2*>(h->W);
+  pw::dense::source_kernel<<<num_sms() * 8, 256, 0, h->stream>>>(sa);
+  pw::dense::AxisArgs ax{};
+  ax.N = N;
+  ax.ncols = (long long)N * N * N;
+  ax.E = h->F;
+  ax.S = h->S;
+  const dim3 grid((unsigned)((ax.ncols + pw::dense::BN - 1) / pw::dense::BN), (unsigned)((N + pw::dense::BM - 1) / pw::dense::BM));
+  float2* Wf = reinterpret_cast<float2*>(h->W);
+  float2* Xf = reinterpret_cast<float2*>(h->work);
+  const long long L[4] = {1, N, (long long)N * N, (long long)N * N * N};
+  for (int pass = 0; pass < 4; ++pass) {
+    ax.L = L[pass];
+    ax.in = pass % 2 == 0 ? Wf : Xf;
+    ax.out = pass % 2 == 0 ? Xf : Wf;
+    ax.scale = pass == 3 ? (float)((d * d / lz) * (d * d / lz)) : 1.0f;
+    if (pass < 2)
+      pw::dense::axis_kernel<false, false><<<grid, pw::dense::NT, 0, h->stream>>>(ax);
+    else if (pass == 2)
+      pw::dense::axis_kernel<true, false><<<grid, pw::dense::NT, 0, h->stream>>>(ax);
+    else
+      pw::dense::axis_kernel<true, true><<<grid, pw::dense::NT, 0, h->stream>>>(ax);
+    if (pass == 1 && ev && (e = cudaEventRecord(ev[1], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "dense propagation launch");
+  if (ev && (e = cudaEventRecord(ev[2], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  h->d = dx;
+  h->kind = SRC_PROPAGATED;
+  h->hermitian = herm ? 1 : 0;
+  h->W0 = nullptr;
+  h->diag = nullptr;
+  h->aperture = 0.0;
+  h->lens_f = 0.0;
+  h->mask = nullptr;
+  return PW_OK;
+}
+
 pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
   if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
   const bool herm = h->kind == SRC_GSM || h->kind == SRC_DIAGONAL || h->hermitian != 0;
+  if (h->Nz > 0 || !supported(h->N)) return propagate_dense(h, z, farfield, herm);
   if (h->N == 256 && !herm)
     return fail(PW_EUNSUPPORTED, "N = 256 needs a Hermitian source (the general strided-store second pass "
                                  "exists for N <= 128 only)");
@@ -582,6 +651,7 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
   if (N < 2 || (N & 1)) return fail(PW_EINVAL, "N must be even and >= 2 (got %d)", N);
   if (!finite_pos(dxi_m)) return fail(PW_EINVAL, "sampling must be finite and > 0 (got %g)", dxi_m);
   if (!finite_pos(lambda_m)) return fail(PW_EINVAL, "wavelength must be finite and > 0 (got %g)", lambda_m);
+  if (N > PW_MAX_N) return fail(PW_EUNSUPPORTED, "no propagation plan for N = %d (at most %d)", N, PW_MAX_N);
   if (!dev_W || !dev_work) return fail(PW_EINVAL, "dev_W and dev_work must be non-null");
   const size_t need = pw_csda_bytes(N);
   if (W_bytes < need || work_bytes < need)
@@ -591,7 +661,6 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
     const char* b0 = reinterpret_cast<const char*>(dev_work);
     if (a0 < b0 + need && b0 < a0 + need) return fail(PW_EINVAL, "dev_W and dev_work overlap");
   }
-  if (!supported(N)) return fail(PW_EUNSUPPORTED, "no propagation plan for N = %d in this build", N);
   pw_csd* h = new pw_csd{};
   h->N = N;
   h->d = dxi_m;
@@ -629,7 +698,7 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
     delete h;
     return cuda_fail(e, "clearing the error flag");
   }
-  pw_status st = make_vmap(h);
+  pw_status st = supported(N) ? make_vmap(h) : PW_OK;  // the dense path needs no tensor map
   if (st != PW_OK) {
     cudaFree(h->tables);
     delete h;
@@ -731,6 +800,22 @@ pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int*
   return PW_OK;
 }
 
+pw_status pw_csd_set_padding(pw_csd* h, int Nz) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (Nz != 0 && (Nz < h->N || (Nz - h->N) % 2 != 0 || Nz > (1 << 20)))
+    return fail(PW_EINVAL, "padded size must be 0 or N <= Nz <= 2^20 with Nz - N even (N = %d, Nz = %d)", h->N, Nz);
+  h->Nz = Nz == h->N ? 0 : Nz;
+  return PW_OK;
+}
+
+pw_status pw_csd_get_padding(const pw_csd* h, int* Nz) {
+  g_err.clear();
+  if (!h || !Nz) return fail(PW_EINVAL, "null argument");
+  *Nz = h->Nz > 0 ? h->Nz : h->N;
+  return PW_OK;
+}
+
 pw_status pw_csd_set_dft_mode(pw_csd* h, int mode) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
@@ -822,6 +907,8 @@ pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double
     return fail(PW_EINVAL, "lengths must be finite and > 0");
   if (!std::isfinite(amplitude)) return fail(PW_EINVAL, "amplitude must be finite");
   if (h->kind != SRC_PROPAGATED) return fail(PW_ESTATE, "no propagated CSDA (run the adjoint propagation first)");
+  if (h->Nz > 0 || !supported(h->N))
+    return fail(PW_EUNSUPPORTED, "the GSM gradient needs an unpadded grid with an FFT plan");
   const int N = h->N;
   const double d = h->d;                    // the source plane of the forward propagation
   const double dx = lambda_m * z_m / (N * d);  // its output plane

@@ -62,7 +62,7 @@ FAKE_W, FAKE_WORK = 0x100000000, 0x900000000  # never dereferenced: validation c
     ((32, float("nan"), 633e-9), "PW_EINVAL", "sampling"),
     ((32, 20e-6, -1.0), "PW_EINVAL", "wavelength"),
     ((32, 20e-6, float("inf")), "PW_EINVAL", "wavelength"),
-    ((10, 20e-6, 633e-9), "PW_EUNSUPPORTED", "N = 10"),
+    ((514, 20e-6, 633e-9), "PW_EUNSUPPORTED", "N = 514"),
 ])
 def test_create_rejects_bad_arguments(lib, args, status, msg):
     N = args[0]
