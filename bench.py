@@ -37,7 +37,8 @@ import workloads as WL  # noqa: E402
 WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
              WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256,
              WL.POLYCHROMATIC_BATCH["name"]: WL.POLYCHROMATIC_BATCH,
-             WL.INVERSE_N96["name"]: WL.INVERSE_N96}
+             WL.INVERSE_N96["name"]: WL.INVERSE_N96,
+             WL.PADDED_PHASE_SCREEN_N200["name"]: WL.PADDED_PHASE_SCREEN_N200}
 DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
 CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
@@ -82,16 +83,26 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample_step(N=SAMPLE_N):
-    """One FP64 oracle propagation of the workload's configuration on an N x N grid,
-    including the source build, S and mu.  Returns the number of points propagated."""
+def sample_n():
+    """Grid (and padded size) of the bounded CPU sample of the workload."""
+    return CFG.get("sample_N", SAMPLE_N), CFG.get("sample_Nz")
+
+
+def oracle_sample_step():
+    """One FP64 oracle propagation of the workload's configuration on the sample grid (zero-padded
+    to the sample's Nz for a padded workload), including the source build, S and mu.  Returns the
+    number of points propagated."""
     import oracle as O
+    N, Nz = sample_n()
     if "corr_px" in CFG:
         m = WL.phase_screen(N, seed=WL.SEED, corr_px=CFG["corr_px"])
     else:
         m = O.circle_aperture(N, CFG["dxi"], CFG["aperture"]) * O.thin_lens(N, CFG["dxi"], CFG["lam"], CFG["lens_f"])
     W0 = O.apply_mask(O.gsm_source(N, CFG["dxi"], CFG["sigma_S"], CFG["sigma_mu"], CFG["A"]), m)
-    W, _ = O.propagate_fft(W0, CFG["dxi"], CFG["lam"], CFG["z"])
+    if Nz:
+        W, _ = O.propagate_padded(W0, CFG["dxi"], CFG["lam"], CFG["z"], Nz)
+    else:
+        W, _ = O.propagate_fft(W0, CFG["dxi"], CFG["lam"], CFG["z"])
     O.spectral_density(W)
     O.degree_of_coherence(W, N // 2, N // 2)
     return N ** 4
@@ -108,20 +119,29 @@ def cpu_baseline(min_s=10.0, max_s=30.0):
         if el >= min_s or el + el / runs > max_s:
             break
     return {"value": pts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 NumPy oracle (single-threaded) on the same configuration at N=%d, %d full "
-                      "propagation(s) incl. source build, S and mu, %.1f s" % (SAMPLE_N, runs, el)}
+            "sample": "FP64 NumPy oracle (single-threaded) on the same configuration at N=%s, %d full "
+                      "propagation(s) incl. source build, S and mu, %.1f s" % (sample_desc(), runs, el)}
 
 
 PLAIN_N_MAX = 128  # largest grid the plain FP32 CPU path runs at (N = 128: 2.1 GB per CSDA copy)
+
+
+def sample_desc():
+    N, Nz = sample_n()
+    return "%d (zero-padded to Nz=%d)" % (N, Nz) if Nz else "%d" % N
 
 
 def cpu_plain_fp32(max_s=30.0):
     """The plain FP32 CPU path (complex64, scipy.fft on every host core) on the workload's
     configuration, at the workload's N up to PLAIN_N_MAX (the same configuration at that grid
     above it).  One untimed propagation at N = 32 first (imports, FFT plans)."""
+    import numpy as np
     import oracle as O
     from oracle import plain_fp32 as P
     N = min(CFG["N"], PLAIN_N_MAX)
+    Nz = None
+    if "Nz" in CFG:  # padded: the sample grid, FFTs at the sample's padded size, output cropped
+        N, Nz = sample_n()
 
     def mask(n):
         if "corr_px" in CFG:
@@ -130,6 +150,13 @@ def cpu_plain_fp32(max_s=30.0):
                                                                                CFG["lens_f"])
 
     def step(n):
+        if Nz and n == N:
+            o = (Nz - N) // 2
+            mp = np.zeros((Nz, Nz), dtype=np.complex128)
+            mp[o:o + N, o:o + N] = mask(N)  # the source on the padded grid, zeros around it
+            W, S, mu, _ = P.propagate_gsm_fp32(Nz, CFG["dxi"], CFG["lam"], CFG["z"], CFG["sigma_S"],
+                                               CFG["sigma_mu"], CFG["A"], mask=mp)
+            return W[o:o + N, o:o + N, o:o + N, o:o + N]
         P.propagate_gsm_fp32(n, CFG["dxi"], CFG["lam"], CFG["z"], CFG["sigma_S"], CFG["sigma_mu"], CFG["A"],
                              mask=mask(n))
 
@@ -143,8 +170,8 @@ def cpu_plain_fp32(max_s=30.0):
             break
     return {"value": runs * N ** 4 / el, "unit": UNIT, "cores": P.host_cores(), "kind": "plain FP32 path",
             "sample": "complex64 array operations + scipy.fft (Algorithm 2 order) on the host cores, the same "
-                      "configuration at N=%d, %d full propagation(s) incl. source build, S and mu, %.1f s"
-                      % (N, runs, el)}
+                      "configuration at N=%s, %d full propagation(s) incl. source build, S and mu, %.1f s"
+                      % ("%d (zero-padded to Nz=%d)" % (N, Nz) if Nz else "%d" % N, runs, el)}
 
 
 def run_reference(args):
@@ -163,10 +190,10 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": CFG["name"], "N": SAMPLE_N, "sample_of_N": CFG["N"]},
+            "config": {"workload": CFG["name"], "N": sample_n()[0], "Nz": sample_n()[1], "sample_of_N": CFG["N"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step: one FP64 oracle propagation of the configuration at "
-                                       "N=%d on the host cores (NumPy, single-threaded)" % SAMPLE_N},
+                                       "N=%s on the host cores (NumPy, single-threaded)" % sample_desc()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -207,6 +234,23 @@ def recorded_traffic(kernel, N):
     if not m or m.group(2) != kernel_source_sha(N):
         return None
     return int(m.group(1))
+
+
+def roofline_alu(N, pts, avg_a, avg_b, clocks):
+    """Padded workloads: the four dense axis contractions are FP32 FMA work, N complex
+    multiply-adds (8 flop) per output point each.  The second pass's events span two
+    contractions.  Peak: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    flops = 8.0 * N * pts
+    avg = avg_b / 2
+    achieved = flops / (avg / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "dense::axis_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (sms, mhz),
+            "traffic": None, "algorithmic_flops_per_launch": flops,
+            "pass_ms": {"pass_a": avg_a, "pass_b": avg_b}}
 
 
 def max_over_ranks(x, dist, device):
@@ -293,6 +337,8 @@ def run_ours(args):
     P1 = CFG["P1"]
     if args.dft == "tc_bf16x3":
         pw.pw_csd_set_dft_mode(h, pw.PW_DFT_TC_BF16X3)
+    if CFG.get("Nz"):
+        pw.pw_csd_set_padding(h, CFG["Nz"])
 
     screen = "corr_px" in CFG
     mask_dev0 = torch.from_numpy(source_mask_host(N)).cuda() if screen else None
@@ -309,7 +355,9 @@ def run_ours(args):
         pw.pw_spectral_density(h, S.data_ptr())
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
 
-    launches_per_step = 5  # tables, pass A, pass B, S kernel, mu kernel
+    # tables, pass A, pass B, S kernel, mu kernel; padded: tables, dense tables, source, four
+    # axis contractions, S kernel, mu kernel
+    launches_per_step = 9 if CFG.get("Nz") else 5
     pw.pw_csd_enable_timing(h, max(args.steps, args.warmup, 1))
     for _ in range(args.warmup):
         step()
@@ -397,7 +445,8 @@ def run_ours(args):
                    "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2: 2 x %.1f GB CSDA buffers stream through HBM every step"
                          % (8 * pts / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": roofline_alu(N, pts, avg_a, avg_b, clocks) if CFG.get("Nz") else
+                    {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern, N),
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "pass_ms": {"pass_a": avg_a, "pass_b": avg_b},

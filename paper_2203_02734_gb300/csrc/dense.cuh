@@ -80,10 +80,12 @@ __global__ void source_kernel(SrcArgs s) {
 }
 
 // One axis contraction, C[k][j] = scale sum_n A(k, n) B[n][j], A = E or conj(E), in FP32.
-// Tile 64 (k) x 64 (j) per CTA of 256 threads, 16 values of n per step through shared memory;
-// thread (ty, tx) = (t / 16, t mod 16) accumulates k = k0 + 4 ty + i, j = j0 + 4 tx + jj (i, jj < 4),
-// so that 16 threads store 64 consecutive columns of one output row.  S_OUT (last pass, L = N^3):
-// S(a', b') = Re C at k = a', j = (b', a', b').
+// Tile 64 (k) x 64 (j) per CTA of 256 threads, 16 values of n per step through shared memory
+// (two buffers: the next step's values are loaded into registers while the current step
+// computes); thread (ty, tx) = (t / 16, t mod 16) accumulates k = k0 + 4 ty + i, j = j0 + 4 tx + jj
+// (i, jj < 4), so that 16 threads store 64 consecutive columns of one output row.  The k tiles of
+// one column tile are consecutive CTAs, so the column block they all read (N x 64) comes from L2
+// after the first.  S_OUT (last pass, L = N^3): S(a', b') = Re C at k = a', j = (b', a', b').
 struct AxisArgs {
   int N;
   long long L;      // elements after the contracted axis
@@ -104,13 +106,14 @@ __device__ __forceinline__ long long col_base(long long j, long long L, int N) {
 
 template <bool CONJ, bool S_OUT>
 __global__ void __launch_bounds__(NT) axis_kernel(AxisArgs p) {
-  __shared__ __align__(16) float2 As[BK][PITCH];
-  __shared__ __align__(16) float2 Bs[BK][PITCH];
+  __shared__ __align__(16) float2 As[2][BK][PITCH];
+  __shared__ __align__(16) float2 Bs[2][BK][PITCH];
   const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
   const int N = p.N;
   const long long L = p.L, ncols = p.ncols;
-  const int k0 = blockIdx.y * BM;
-  const long long j0 = (long long)blockIdx.x * BN;
+  const int ktiles = (N + BM - 1) / BM;
+  const int k0 = (int)(blockIdx.x % ktiles) * BM;
+  const long long j0 = (long long)(blockIdx.x / ktiles) * BN;
   // B loads: L > 1 -> column jl = t mod 64 fixed, rows kk = t / 64 + 4 i (contiguous columns);
   //          L = 1 -> row kk = t mod 16 fixed, columns jl = t / 16 + 16 i (contiguous rows).
   const bool rowwise = L == 1;
@@ -123,32 +126,43 @@ __global__ void __launch_bounds__(NT) axis_kernel(AxisArgs p) {
     const long long j = j0 + bj[i];
     bbase[i] = j < ncols ? col_base(j, L, N) : -1;
   }
+  float2 ra[4], rb[4];
+  auto load = [&](int n0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // A: 64 x 16, n fastest
+      const int e = t + NT * i, kk = e & 15, kl = e >> 4;
+      const int k = k0 + kl, n = n0 + kk;
+      ra[i] = (k < N && n < N) ? p.E[k * N + n] : make_float2(0.f, 0.f);
+      if (CONJ) ra[i].y = -ra[i].y;
+      const int nb = n0 + bk[i];
+      rb[i] = (bbase[i] >= 0 && nb < N) ? p.in[bbase[i] + (long long)nb * L] : make_float2(0.f, 0.f);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = t + NT * i;
+      As[buf][e & 15][e >> 4] = ra[i];
+      Bs[buf][bk[i]][bj[i]] = rb[i];
+    }
+  };
   float2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) acc[i][jj] = make_float2(0.f, 0.f);
-  for (int n0 = 0; n0 < N; n0 += BK) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {  // A: 64 x 16, n fastest
-      const int e = t + NT * i, kk = e & 15, kl = e >> 4;
-      const int k = k0 + kl, n = n0 + kk;
-      float2 v = (k < N && n < N) ? p.E[k * N + n] : make_float2(0.f, 0.f);
-      if (CONJ) v.y = -v.y;
-      As[kk][kl] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int n = n0 + bk[i];
-      Bs[bk[i]][bj[i]] = (bbase[i] >= 0 && n < N) ? p.in[bbase[i] + (long long)n * L] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int n0 = 0, buf = 0; n0 < N; n0 += BK, buf ^= 1) {
+    const bool more = n0 + BK < N;
+    if (more) load(n0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 a01 = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
-      const float4 a23 = *reinterpret_cast<const float4*>(&As[kk][4 * ty + 2]);
-      const float4 b01 = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
-      const float4 b23 = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx + 2]);
+      const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+      const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty + 2]);
+      const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+      const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx + 2]);
       const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
                            make_float2(a23.z, a23.w)};
       const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
@@ -161,6 +175,7 @@ __global__ void __launch_bounds__(NT) axis_kernel(AxisArgs p) {
           acc[i][jj].y = fmaf(a[i].x, b[jj].y, fmaf(a[i].y, b[jj].x, acc[i][jj].y));
         }
     }
+    if (more) store(buf ^ 1);  // buffer buf ^ 1 was last read before the previous barrier
     __syncthreads();
   }
   const long long NN = (long long)N * N;

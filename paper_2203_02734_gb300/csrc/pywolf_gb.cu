@@ -456,7 +456,7 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   ax.ncols = (long long)N * N * N;
   ax.E = h->F;
   ax.S = h->S;
-  const dim3 grid((unsigned)((ax.ncols + pw::dense::BN - 1) / pw::dense::BN), (unsigned)((N + pw::dense::BM - 1) / pw::dense::BM));
+  const dim3 grid((unsigned)(((ax.ncols + pw::dense::BN - 1) / pw::dense::BN) * ((N + pw::dense::BM - 1) / pw::dense::BM)));
   float2* Wf = reinterpret_cast<float2*>(h->W);
   float2* Xf = reinterpret_cast<float2*>(h->work);
   const long long L[4] = {1, N, (long long)N * N, (long long)N * N * N};

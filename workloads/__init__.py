@@ -32,6 +32,11 @@ POLYCHROMATIC_BATCH = dict(name="polychromatic_batch", Ns=(64, 96, 128), zs=(0.1
 PHASE_SCREEN_N256 = dict(name="phase_screen_gsm_n256", N=256, dxi=20e-6, lam=633e-9,
                          sigma_S=0.1e-3, sigma_mu=0.05e-3, A=1.0, z=0.5, corr_px=3.0,
                          P1=(128, 128))
+# Zero padding with cropped output at the paper's padded sizes (Sec. 5.1 / 5.2 use N = 200 and
+# Nz = 512): the N = 256 workload's phase-screen GSM source on that grid.
+PADDED_PHASE_SCREEN_N200 = dict(name="padded_phase_screen_gsm_n200", N=200, Nz=512, dxi=20e-6,
+                                lam=633e-9, sigma_S=0.1e-3, sigma_mu=0.05e-3, A=1.0, z=0.5,
+                                corr_px=3.0, P1=(100, 100), sample_N=24, sample_Nz=62)
 INVERSE_N96 = dict(name="amplitude_mask_gsm_n96", N=96, dxi=20e-6, lam=633e-9, sigma_S=0.1e-3,
                    sigma_mu=0.05e-3, A=1.0, z=1.0, P1=(48, 48))
 
