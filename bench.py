@@ -54,9 +54,10 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
                    help="default: the N = 128 workload the metric is quoted on")
-    p.add_argument("--dft", choices=["fp32", "tc_bf16x3"], default="fp32",
-                   help="N = 256 only: the first pass's first radix-16 stage as FP32 codelets (default) or on "
-                        "the tensor cores with split-BF16x3 operands")
+    p.add_argument("--dft", choices=["auto", "fp32", "tc_bf16x3"], default="auto",
+                   help="arithmetic of the DFT work with a tensor-core form (the N = 256 first stage, the dense "
+                        "contractions of padded workloads): auto (the library's per-path default), FP32 on the "
+                        "CUDA cores, or split-BF16x3 on the tensor cores")
     a = p.parse_args()
     global CFG
     CFG = WORKLOADS[a.workload]
@@ -236,20 +237,37 @@ def recorded_traffic(kernel, N):
     return int(m.group(1))
 
 
-def roofline_alu(N, pts, avg_a, avg_b, clocks):
-    """Padded workloads: the four dense axis contractions are FP32 FMA work, N complex
-    multiply-adds (8 flop) per output point each.  The second pass's events span two
-    contractions.  Peak: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock."""
+def roofline_dense(N, pts, avg_a, avg_b, clocks, tc):
+    """Padded workloads: four dense axis contractions, N complex multiply-adds (8 flop) per output
+    point each; the second pass's events span two contractions.
+    CUDA cores (tc False): FP32 FMA work against SMs x 128 FP32 lanes x 2 flop x the maximum SM clock.
+    Tensor cores (tc True): the BF16 MMA flops one launch issues, ceil(N^3 / 128) tiles x
+    Np / 16 chunks x 24 MMAs of 2 x 128 x Np x 16 flop (Np = N rounded up to 16; six split products),
+    against the measured BF16 peak."""
     import torch
+    avg = avg_b / 2
+    fp32_flops = 8.0 * N * pts
+    if tc:
+        Np = (N + 15) // 16 * 16
+        tiles = (N ** 3 + 127) // 128
+        flops = tiles * (Np // 16) * 24 * 2.0 * 128 * Np * 16
+        try:
+            peak, src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]), "measured"
+        except Exception:
+            peak, src = 1900.0, "fallback"
+        achieved = flops / (avg / 1e3) / 1e12
+        return {"bound": "tensor", "kernel": "dense_tc::axis_tc_kernel", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src + " (bf16, burst)", "traffic": None,
+                "algorithmic_flops_per_launch": flops,
+                "fp32_equivalent_tflops": fp32_flops / (avg / 1e3) / 1e12,
+                "pass_ms": {"pass_a": avg_a, "pass_b": avg_b}}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * mhz * 1e6 / 1e12
-    flops = 8.0 * N * pts
-    avg = avg_b / 2
-    achieved = flops / (avg / 1e3) / 1e12
+    achieved = fp32_flops / (avg / 1e3) / 1e12
     return {"bound": "alu", "kernel": "dense::axis_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (sms, mhz),
-            "traffic": None, "algorithmic_flops_per_launch": flops,
+            "traffic": None, "algorithmic_flops_per_launch": fp32_flops,
             "pass_ms": {"pass_a": avg_a, "pass_b": avg_b}}
 
 
@@ -335,8 +353,8 @@ def run_ours(args):
     c = pw.CSD(N, CFG["dxi"], CFG["lam"], W=W, work=work, stream=stream)
     h = c.h
     P1 = CFG["P1"]
-    if args.dft == "tc_bf16x3":
-        pw.pw_csd_set_dft_mode(h, pw.PW_DFT_TC_BF16X3)
+    pw.pw_csd_set_dft_mode(h, {"auto": pw.PW_DFT_AUTO, "fp32": pw.PW_DFT_FP32,
+                               "tc_bf16x3": pw.PW_DFT_TC_BF16X3}[args.dft])
     if CFG.get("Nz"):
         pw.pw_csd_set_padding(h, CFG["Nz"])
 
@@ -356,8 +374,8 @@ def run_ours(args):
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
 
     # tables, pass A, pass B, S kernel, mu kernel; padded: tables, dense tables, source, four
-    # axis contractions, S kernel, mu kernel
-    launches_per_step = 9 if CFG.get("Nz") else 5
+    # axis contractions (+ two matrix splits on the tensor cores), S kernel, mu kernel
+    launches_per_step = (11 if args.dft != "fp32" and N <= 256 else 9) if CFG.get("Nz") else 5
     pw.pw_csd_enable_timing(h, max(args.steps, args.warmup, 1))
     for _ in range(args.warmup):
         step()
@@ -445,7 +463,7 @@ def run_ours(args):
                    "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2: 2 x %.1f GB CSDA buffers stream through HBM every step"
                          % (8 * pts / 1e9)},
-        "roofline": roofline_alu(N, pts, avg_a, avg_b, clocks) if CFG.get("Nz") else
+        "roofline": roofline_dense(N, pts, avg_a, avg_b, clocks, args.dft != "fp32" and N <= 256) if CFG.get("Nz") else
                     {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern, N),
                      "algorithmic_bytes_per_launch": bytes_launch,

@@ -183,25 +183,29 @@ pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu);
  * contractions in FP32: the pruned DFT of size Nz with the propagators folded in, one N x N
  * complex matrix per axis (O(N) work per point instead of O(log N)).  It accepts every source
  * (GSM, uploaded CSDA, diagonal, propagated plane, with masks), produces the same outputs
- * (W, S, mu) and ignores pw_csd_set_dft_mode.
+ * (W, S, mu); its arithmetic follows pw_csd_set_dft_mode.
  * Returns PW_EINVAL for Nz < N (other than 0), odd Nz - N or Nz > 1 << 20; kept across
  * pw_csd_reset. */
 pw_status pw_csd_set_padding(pw_csd* h, int Nz);
 pw_status pw_csd_get_padding(const pw_csd* h, int* Nz);
 
-/* Arithmetic of the first radix-16 DFT stage of the first pass at N = 256 (all other stages
- * and grid sizes always run FP32 codelets on the CUDA cores; the DFT itself is Algorithm 2's
- * direct 2D transform over the point-2 pair).
- *   PW_DFT_FP32 (default): FP32 complex codelet with FP64-derived twiddles.
- *   PW_DFT_TC_BF16X3: the stage as a GEMM on the tensor cores (tcgen05, BF16 operands, FP32
- *     accumulation): each FP32 operand split into three BF16 parts, six partial products kept
- *     (relative error of the stage ~5e-7).  A comparison mode, not a faster one: the split and the
- *     tensor-memory round trip cost more than the codelet.
- * Returns PW_EINVAL for an unknown mode, PW_EUNSUPPORTED for PW_DFT_TC_BF16X3 at N != 256.  A
- * later propagation of a source other than the Gaussian Schell model (with or without masks)
- * returns PW_EUNSUPPORTED while the tensor-core mode is set.  A bounded device wait of the
- * tensor-core stage that gives up is reported by pw_csd_check (PW_ETIMEOUT). */
-enum { PW_DFT_FP32 = 0, PW_DFT_TC_BF16X3 = 1 };
+/* Arithmetic of the DFT work that has a tensor-core form:
+ *   - the first radix-16 stage of the first pass at N = 256 (FFT path, GSM sources; all other
+ *     stages and FFT grid sizes always run FP32 codelets on the CUDA cores), and
+ *   - the four dense axis contractions of the padded / no-FFT-plan path (N <= 256).
+ *   PW_DFT_AUTO (default): the faster of the two per path, as measured on GB300: FP32 codelets on
+ *     the FFT paths, the tensor cores for the dense contractions (N <= 256; FP32 above).
+ *   PW_DFT_FP32: FP32 on the CUDA cores everywhere (codelets with FP64-derived twiddles, dense FP32
+ *     complex products).
+ *   PW_DFT_TC_BF16X3: the products as GEMMs on the tensor cores (tcgen05, BF16 operands,
+ *     FP32 accumulation in tensor memory), each FP32 operand split into three BF16 parts and six
+ *     partial products kept (relative error ~5e-7 per stage).
+ * Returns PW_EINVAL for an unknown mode, PW_EUNSUPPORTED for PW_DFT_TC_BF16X3 at N > 256.  On the
+ * FFT path at N = 256 a later propagation of a source other than the Gaussian Schell model
+ * returns PW_EUNSUPPORTED while the tensor-core mode is set; at other FFT grid sizes the mode has
+ * no effect.  A bounded device wait of a tensor-core kernel that gives up is reported by
+ * pw_csd_check (PW_ETIMEOUT). */
+enum { PW_DFT_AUTO = 0, PW_DFT_FP32 = 1, PW_DFT_TC_BF16X3 = 2 };
 pw_status pw_csd_set_dft_mode(pw_csd* h, int mode);
 pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode);
 

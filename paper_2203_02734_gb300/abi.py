@@ -134,7 +134,7 @@ def pw_csd_reset(h, dxi_m):
     _check(LIB.pw_csd_reset(h, dxi_m))
 
 
-PW_DFT_FP32, PW_DFT_TC_BF16X3 = 0, 1
+PW_DFT_AUTO, PW_DFT_FP32, PW_DFT_TC_BF16X3 = 0, 1, 2
 PW_MAX_N = 512
 
 

@@ -1,0 +1,246 @@
+// dense_tc.cuh -- the dense axis contraction of dense.cuh on the tensor cores (tcgen05.mma,
+// kind::f16, BF16 operands split in three, FP32 accumulators in tensor memory), N <= 256.
+//
+// C[k][j] = scale sum_n A(k, n) B[n][j] as a real GEMM D = X Q^T per tile of 128 columns j:
+//   X (128 x 2Np): row = column j, (Re B[n][j], Im B[n][j]) at 2n, 2n + 1 (zero for n >= N);
+//   Q (2Np x 2Np): Q(2k, 2n) = Re A, Q(2k, 2n+1) = -Im A, Q(2k+1, 2n) = Im A, Q(2k+1, 2n+1) = Re A;
+//   D (128 x 2Np FP32, tensor memory lanes x columns): (Re C[k][j], Im C[k][j]) at 2k, 2k + 1;
+// Np = N rounded up to 16.  Both operands are split in three BF16 parts and D accumulates the six
+// products of tc16.cuh.  K runs in chunks of 16 complex inputs (32 reals, two MMA K-steps); the
+// output reals run in two halves of Np (the MMA's N <= 256), so a chunk is 6 x 2 x 2 = 24 MMAs.
+//
+// Q is split once per propagation by qsplit_kernel into a global buffer laid out chunk by chunk
+// in the canonical K-major layout (no swizzle): per chunk, split s and K-step ks, core matrices
+// [kb < 2][row group < 2Np / 8] of 8 rows x 16 bytes, so one chunk is 384 Np contiguous bytes and
+// arrives by bulk copies.  Two chunk buffers: the copy of chunk c + 1 overlaps the MMAs of
+// chunk c.  The A tile (24 KB) is rebuilt per chunk by all 256 threads (thread t: column t mod
+// 128, K-step t / 128) once the previous chunk's MMAs have read it; its global loads are issued
+// before that wait.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "dense.cuh"
+#include "tc16.cuh"
+
+namespace pw {
+namespace dense_tc {
+
+constexpr int NT = 256;
+constexpr int MAX_N = 256;
+
+__host__ __device__ constexpr int npad(int N) { return (N + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t chunk_bytes(int N) { return (size_t)384 * npad(N); }
+__host__ __device__ constexpr int nchunks(int N) { return npad(N) / 16; }
+constexpr uint32_t A_BYTES = 3 * 2 * 4096;  // 3 splits x 2 K-steps x (128 rows x 16 bf16)
+__host__ __device__ constexpr size_t smem_bytes(int N) { return A_BYTES + 2 * chunk_bytes(N) + 64; }
+// Tensor-memory columns to allocate: a power of two >= 32 holding D's 2 Np columns.
+__host__ __device__ constexpr uint32_t tmem_cols(int N) {
+  return 2 * npad(N) <= 32 ? 32 : 2 * npad(N) <= 64 ? 64 : 2 * npad(N) <= 128 ? 128 : 2 * npad(N) <= 256 ? 256 : 512;
+}
+
+// Instruction descriptor: D FP32, A and B BF16, K-major, M = 128, N = Np.
+__host__ __device__ constexpr uint32_t idesc(int Np) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// Split Q for chunk c: element (row r < 2Np, K index kk < 32 of the chunk) of split s goes to
+// chunk c, block (s, ks = kk / 16), core matrix (kb = (kk mod 16) / 8, row group r / 8).
+struct QArgs {
+  int N;
+  const float2* E;  // N x N, row k, column n
+  int conj;         // A = conj(E)
+  __nv_bfloat16* Q; // nchunks x chunk_bytes
+};
+
+__global__ void qsplit_kernel(QArgs a) {
+  const int N = a.N, Np = npad(N), R = 2 * Np;
+  const int total = nchunks(N) * R * 32;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int c = idx / (R * 32), rem = idx - c * R * 32, r = rem / 32, kk = rem - r * 32;
+    const int k = r >> 1, cp = r & 1, n = c * 16 + (kk >> 1), cc = kk & 1;
+    float v = 0.f;
+    if (k < N && n < N) {
+      float2 e = a.E[k * N + n];
+      if (a.conj) e.y = -e.y;
+      v = cp == 0 ? (cc == 0 ? e.x : -e.y) : (cc == 0 ? e.y : e.x);
+    }
+    const __nv_bfloat16 s1 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(s1);
+    const __nv_bfloat16 s2 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 s3 = __float2bfloat16_rn(r1 - __bfloat162float(s2));
+    const int ks = kk >> 4, kb = (kk >> 3) & 1, e8 = kk & 7;
+    const size_t block = (size_t)64 * Np;  // bytes of one (split, K-step) block
+    const size_t off = (size_t)c * chunk_bytes(N) + (size_t)ks * block +
+                       (size_t)((kb * (R / 8) + (r >> 3)) * 128 + (r & 7) * 16 + e8 * 2);
+    unsigned char* base = reinterpret_cast<unsigned char*>(a.Q);
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = s1;
+    *reinterpret_cast<__nv_bfloat16*>(base + off + 2 * block) = s2;
+    *reinterpret_cast<__nv_bfloat16*>(base + off + 4 * block) = s3;
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mma_np(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}" ::"r"(d),
+               "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld16(float (&r)[16], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+        "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One tile of 128 columns j per CTA (grid = ceil(N^3 / 128)), 256 threads; tmem_cols(N)
+// tensor-memory columns and 2 x chunk + 24 KB of shared memory (one CTA per SM at N = 200).  A bounded wait that gives up
+// sets *err; the tile's outputs are then not written.
+template <bool S_OUT>
+__global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const unsigned char* __restrict__ Q,
+                                                         int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int N = p.N, Np = npad(N), nch = nchunks(N);
+  const uint32_t cb = (uint32_t)chunk_bytes(N);
+  unsigned char* As = sm;
+  unsigned char* Bs0 = sm + A_BYTES;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(sm + A_BYTES + 2 * cb);  // [2]
+  uint64_t* mdone = bfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  const int t = threadIdx.x, w = t >> 5, m = t & 127, ks = t >> 7;
+  const long long L = p.L, ncols = p.ncols;
+  const long long j = (long long)blockIdx.x * 128 + m;
+  const long long jb = j < ncols ? dense::col_base(j, L, N) : -1;
+
+  if (w == 0) tc16::tmem_alloc(tslot, tmem_cols(N));
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mdone)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc16::fence_before_sync();
+  __syncthreads();
+  tc16::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc(Np);
+  auto load_chunk = [&](int c) {  // one thread
+    unsigned char* dst = Bs0 + (c & 1) * cb;
+    const unsigned char* src = Q + (size_t)c * cb;
+    mbar_expect_tx(&bfull[c & 1], cb);
+    const uint32_t piece = cb / 4;  // 96 Np bytes, a multiple of 16
+    for (int q = 0; q < 4; ++q) bulk_g2s(dst + q * piece, src + (size_t)q * piece, piece, &bfull[c & 1]);
+  };
+  if (t == 0) {
+    load_chunk(0);
+    if (nch > 1) load_chunk(1);
+  }
+  bool ok = true;
+  for (int c = 0; c < nch; ++c) {
+    // the thread's 8 inputs n = 16 c + 8 ks + i of column j, loaded before the wait below
+    float2 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = 16 * c + 8 * ks + i;
+      x[i] = (jb >= 0 && n < N) ? p.in[jb + (long long)n * L] : make_float2(0.f, 0.f);
+    }
+    int okv = 1;
+    if (c > 0 && t == 0) {
+      okv = ok && tc16::mbar_wait(mdone, (uint32_t)((c - 1) & 1));  // chunk c-1 read A and its B buffer
+      if (okv && c + 1 < nch) load_chunk(c + 1);
+    }
+    ok = __syncthreads_and(okv) != 0 && ok;
+    // split into three BF16 parts: row m, K-step ks, core matrices kb = 0, 1 (4 complex each)
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+      uint32_t wv[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 v = x[4 * kb + q];
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.x, v.y);
+        const float rx = v.x - __low2float(h1), ry = v.y - __high2float(h1);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(rx, ry);
+        const __nv_bfloat162 h3 = __floats2bfloat162_rn(rx - __low2float(h2), ry - __high2float(h2));
+        wv[0][q] = tc16::bf2_bits(h1);
+        wv[1][q] = tc16::bf2_bits(h2);
+        wv[2][q] = tc16::bf2_bits(h3);
+      }
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+        *reinterpret_cast<uint4*>(As + sp * 8192 + ks * 4096 + (kb * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
+            make_uint4(wv[sp][0], wv[sp][1], wv[sp][2], wv[sp][3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc16::fence_before_sync();
+    __syncthreads();
+    if (t == 0 && ok) {
+      ok = tc16::mbar_wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1));
+      if (ok) {
+        tc16::fence_after_sync();
+        constexpr int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
+        const uint64_t a0 = tc16::sdesc(smem_u32(As), 2048, 128);
+        const uint64_t b0 = tc16::sdesc(smem_u32(Bs0 + (c & 1) * cb), (uint32_t)(32 * Np), 128);
+        const uint32_t blk = (uint32_t)(64 * Np);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t ad = a0 + (uint64_t)((ti[q] * 8192 + s2 * 4096) >> 4);
+              const uint64_t bd = b0 + (uint64_t)(((tj[q] * 2 + s2) * blk + h * (Np / 8) * 128) >> 4);
+              mma_np(tmem + (uint32_t)(h * Np), ad, bd, id, (c | q | s2) ? 1u : 0u);
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(mdone))
+                     : "memory");
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+  }
+  int okv = 1;
+  if (t == 0) okv = ok && tc16::mbar_wait(mdone, (uint32_t)((nch - 1) & 1));
+  ok = __syncthreads_and(okv) != 0;
+  tc16::fence_after_sync();
+  if (ok) {
+    // warp w reads lanes 32 (w mod 4) .. + 31 (columns j) of output half w / 4
+    const int h = w >> 2;
+    const long long NN = (long long)N * N;
+    for (int q = 0; q < Np / 16; ++q) {  // 16 columns (8 complex outputs) per load, Np per half
+      float r[16];
+      tmem_ld16(r, tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(h * Np + 16 * q));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = (h * Np + 16 * q) / 2 + i;
+        if (jb >= 0 && k < N) {
+          const float2 v = make_float2(r[2 * i] * p.scale, r[2 * i + 1] * p.scale);
+          p.out[jb + (long long)k * L] = v;
+          if (S_OUT) {
+            const int b = (int)(j / NN), cc = (int)((j / N) % N), d = (int)(j % N);
+            if (cc == k && d == b) p.S[k * N + b] = v.x;
+          }
+        }
+      }
+    }
+  } else if (t == 0) {
+    atomicExch(err, 1);
+  }
+  tc16::fence_before_sync();
+  __syncthreads();
+  if (w == 0) tc16::tmem_dealloc(tmem, tmem_cols(N));
+}
+
+}  // namespace dense_tc
+}  // namespace pw

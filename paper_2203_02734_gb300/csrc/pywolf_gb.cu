@@ -15,6 +15,7 @@
 #include "propagate.cuh"
 #include "d256.cuh"
 #include "dense.cuh"
+#include "dense_tc.cuh"
 #include "grad.cuh"
 #include "r128.cuh"
 #include "r96.cuh"
@@ -80,8 +81,9 @@ struct pw_csd {
   float* S;       // S of the last propagated plane (pass-B epilogue)
   int* err;       // device flag: a bounded wait in a kernel gave up
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
-  int dft_mode;      // PW_DFT_FP32 or PW_DFT_TC_BF16X3 (N = 256 first pass, first stage)
+  int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
+  void* qbuf;        // split DFT matrices of the tensor-core dense path (allocated on first use)
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
   int timed;
@@ -460,7 +462,40 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   float2* Wf = reinterpret_cast<float2*>(h->W);
   float2* Xf = reinterpret_cast<float2*>(h->work);
   const long long L[4] = {1, N, (long long)N * N, (long long)N * N * N};
-  for (int pass = 0; pass < 4; ++pass) {
+  const bool tc = h->dft_mode != PW_DFT_FP32 && N <= pw::dense_tc::MAX_N;
+  if (tc) {  // the split matrices of E (point 2) and conj(E) (point 1), then four tensor-core passes
+    const size_t qb = (size_t)pw::dense_tc::nchunks(N) * pw::dense_tc::chunk_bytes(N);
+    if (!h->qbuf && (e = cudaMalloc(&h->qbuf, 2 * qb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc of the split DFT matrices");
+    static size_t smem_set = 0;
+    const size_t smem = pw::dense_tc::smem_bytes(N);
+    if (smem > smem_set) {
+      if ((e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return cuda_fail(e, "shared memory of the tensor-core contraction");
+      smem_set = smem;
+    }
+    unsigned char* q = reinterpret_cast<unsigned char*>(h->qbuf);
+    for (int cj = 0; cj < 2; ++cj) {
+      pw::dense_tc::QArgs qa{N, h->F, cj, reinterpret_cast<__nv_bfloat16*>(q + cj * qb)};
+      pw::dense_tc::qsplit_kernel<<<num_sms() * 4, 256, 0, h->stream>>>(qa);
+    }
+    const dim3 tgrid((unsigned)((ax.ncols + 127) / 128));
+    for (int pass = 0; pass < 4; ++pass) {
+      ax.L = L[pass];
+      ax.in = pass % 2 == 0 ? Wf : Xf;
+      ax.out = pass % 2 == 0 ? Xf : Wf;
+      ax.scale = pass == 3 ? (float)((d * d / lz) * (d * d / lz)) : 1.0f;
+      const unsigned char* qm = q + (pass < 2 ? 0 : qb);
+      if (pass < 3)
+        pw::dense_tc::axis_tc_kernel<false><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+      else
+        pw::dense_tc::axis_tc_kernel<true><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+      if (pass == 1 && ev && (e = cudaEventRecord(ev[1], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+    }
+  }
+  for (int pass = 0; pass < 4 && !tc; ++pass) {
     ax.L = L[pass];
     ax.in = pass % 2 == 0 ? Wf : Xf;
     ax.out = pass % 2 == 0 ? Xf : Wf;
@@ -720,6 +755,7 @@ pw_status pw_csd_destroy(pw_csd* h) {
   cudaError_t e1 = cudaStreamSynchronize(h->stream);
   free_events(h);
   cudaError_t e2 = cudaFree(h->tables);
+  if (h->qbuf) cudaFree(h->qbuf);
   delete h;
   if (e1 != cudaSuccess) return cuda_fail(e1, "stream synchronize in destroy");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFree of the handle tables");
@@ -819,9 +855,10 @@ pw_status pw_csd_get_padding(const pw_csd* h, int* Nz) {
 pw_status pw_csd_set_dft_mode(pw_csd* h, int mode) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
-  if (mode != PW_DFT_FP32 && mode != PW_DFT_TC_BF16X3) return fail(PW_EINVAL, "unknown DFT mode %d", mode);
-  if (mode == PW_DFT_TC_BF16X3 && h->N != 256)
-    return fail(PW_EUNSUPPORTED, "the tensor-core stage exists for N = 256 only (N = %d)", h->N);
+  if (mode != PW_DFT_AUTO && mode != PW_DFT_FP32 && mode != PW_DFT_TC_BF16X3)
+    return fail(PW_EINVAL, "unknown DFT mode %d", mode);
+  if (mode == PW_DFT_TC_BF16X3 && h->N > pw::dense_tc::MAX_N)
+    return fail(PW_EUNSUPPORTED, "the tensor-core paths exist for N <= %d (N = %d)", pw::dense_tc::MAX_N, h->N);
   h->dft_mode = mode;
   return PW_OK;
 }

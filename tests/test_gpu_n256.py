@@ -136,8 +136,10 @@ def test_dft_mode_arguments():
     with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
         pw.pw_propagate_fresnel(c.h, 0.5)
     c.close()
-    c = pw.CSD(64, 20e-6, 633e-9)
+    # N = 300 (dense path, above the tensor-core limit): buffers that are never touched
+    nb = pw.pw_csda_bytes(300)
+    h = pw.pw_csd_create(300, 20e-6, 633e-9, 1 << 40, nb, (1 << 40) + nb, nb)
     with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
-        pw.pw_csd_set_dft_mode(c.h, pw.PW_DFT_TC_BF16X3)
-    assert pw.pw_csd_get_dft_mode(c.h) == pw.PW_DFT_FP32
-    c.close()
+        pw.pw_csd_set_dft_mode(h, pw.PW_DFT_TC_BF16X3)
+    assert pw.pw_csd_get_dft_mode(h) == pw.PW_DFT_AUTO
+    pw.pw_csd_destroy(h)

@@ -1,7 +1,8 @@
 """Zero padding with cropped output (Sec. 3.2) and grid sizes without an FFT plan: the dense path
-(four axis contractions) against the FP64 oracle's padded route, element by element at small N,
-by row probes at the paper's N = 200 / Nz = 512, and the paper's own padded examples of Sec. 5.1
-and 5.2 (N = 200, Nz = 512, the paper's parameters) against their closed forms (GPU)."""
+(four axis contractions, FP32 on the CUDA cores or split-BF16x3 on the tensor cores) against the
+FP64 oracle's padded route, element by element at small N, by row probes at the paper's
+N = 200 / Nz = 512, and the paper's own padded examples of Sec. 5.1 and 5.2 (N = 200, Nz = 512,
+the paper's parameters) against their closed forms (GPU)."""
 import numpy as np
 import pytest
 
@@ -11,17 +12,19 @@ import workloads as WL
 pytestmark = pytest.mark.gpu
 
 D, LAM, SS, SM = 20e-6, 633e-9, 0.1e-3, 0.05e-3
+MODES = pytest.mark.parametrize("mode", [1, 2], ids=["fp32", "tc_bf16x3"])  # PW_DFT_FP32, PW_DFT_TC_BF16X3
 
 
 def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-def _gpu(N, Nz, setup, z, farfield=False, dxi=D, lam=LAM):
+def _gpu(N, Nz, setup, z, farfield=False, dxi=D, lam=LAM, mode=1):
     import torch
     import paper_2203_02734_gb300 as pw
     c = pw.CSD(N, dxi, lam)
     pw.pw_csd_set_padding(c.h, Nz)
+    pw.pw_csd_set_dft_mode(c.h, mode)
     assert pw.pw_csd_get_padding(c.h) == Nz
     keep = setup(c, pw, torch)
     (c.propagate_farfield if farfield else c.propagate_fresnel)(z)
@@ -46,34 +49,37 @@ def _check(W, S, mu, dx, Wr, dxr):
     assert np.abs(mu - mur)[keep].max() < 1e-4
 
 
-@pytest.mark.parametrize("N,Nz,farfield", [(16, 24, False), (16, 40, True), (12, 30, False)])
-def test_padded_gsm_aperture_lens(N, Nz, farfield):
+@MODES
+@pytest.mark.parametrize("N,Nz,farfield", [(16, 24, False), (16, 40, True), (12, 30, False), (40, 64, False)])
+def test_padded_gsm_aperture_lens(N, Nz, farfield, mode):
     radius, f, z = 0.3 * N * D, 0.3, 0.4
 
     def setup(c, pw, torch):
         c.source_gsm(SS, SM, 1.0)
         c.source_aperture(radius)
         c.source_lens(f)
-    W, S, mu, dx = _gpu(N, Nz, setup, z, farfield)
+    W, S, mu, dx = _gpu(N, Nz, setup, z, farfield, mode=mode)
     m = O.circle_aperture(N, D, radius) * O.thin_lens(N, D, LAM, f)
     Wr, dxr = O.propagate_padded(O.apply_mask(O.gsm_source(N, D, SS, SM), m), D, LAM, z, Nz, farfield)
     _check(W, S, mu, dx, Wr, dxr)
 
 
-def test_no_fft_plan_grid_unpadded():
+@MODES
+def test_no_fft_plan_grid_unpadded(mode):
     # N = 20 has no FFT plan: the dense path computes Algorithm 2's result at size N
     N = 20
 
     def setup(c, pw, torch):
         c.source_gsm(SS, SM, 1.0)
         c.source_aperture(0.3 * N * D)
-    W, S, mu, dx = _gpu(N, N, setup, 0.5)
+    W, S, mu, dx = _gpu(N, N, setup, 0.5, mode=mode)
     Wr, dxr = O.propagate_fft(O.apply_mask(O.gsm_source(N, D, SS, SM), O.circle_aperture(N, D, 0.3 * N * D)),
                               D, LAM, 0.5)
     _check(W, S, mu, dx, Wr, dxr)
 
 
-def test_padded_uploaded_non_hermitian_array():
+@MODES
+def test_padded_uploaded_non_hermitian_array(mode):
     N, Nz = 12, 20
     rng = np.random.default_rng(11)
     W0 = (rng.standard_normal((N,) * 4) + 1j * rng.standard_normal((N,) * 4)).astype(np.complex64)
@@ -81,13 +87,14 @@ def test_padded_uploaded_non_hermitian_array():
     def setup(c, pw, torch):
         c.W.copy_(torch.from_numpy(W0).cuda())
         pw.pw_source_array(c.h, c.W.data_ptr(), False)
-    W, S, mu, dx = _gpu(N, Nz, setup, 0.5)
+    W, S, mu, dx = _gpu(N, Nz, setup, 0.5, mode=mode)
     Wr, dxr = O.propagate_padded(W0.astype(np.complex128), D, LAM, 0.5, Nz)
     assert dx == pytest.approx(dxr, rel=1e-12)
     assert rel(W, Wr) < 1e-5
 
 
-def test_padded_diagonal_source():
+@MODES
+def test_padded_diagonal_source(mode):
     N, Nz = 16, 28
     d = WL.amplitude_mask(N, seed=5).real.astype(np.float32)
 
@@ -95,7 +102,7 @@ def test_padded_diagonal_source():
         dd = torch.from_numpy(d).cuda()
         pw.pw_source_diagonal(c.h, dd.data_ptr(), 1.0)
         return dd
-    W, S, mu, dx = _gpu(N, Nz, setup, 2.0, farfield=True)
+    W, S, mu, dx = _gpu(N, Nz, setup, 2.0, farfield=True, mode=mode)
     W0 = np.zeros((N,) * 4, dtype=np.complex128)
     i = np.arange(N)
     W0[i[:, None], i[None, :], i[:, None], i[None, :]] = d
@@ -136,14 +143,16 @@ def test_padding_arguments():
     c.close()
 
 
-def _paper_handle(N, Nz, dxi, lam):
+def _paper_handle(N, Nz, dxi, lam, mode=1):
     import paper_2203_02734_gb300 as pw
     c = pw.CSD(N, dxi, lam)
     pw.pw_csd_set_padding(c.h, Nz)
+    pw.pw_csd_set_dft_mode(c.h, mode)
     return c, pw
 
 
-def test_paper_dark_spot_n200_nz512():
+@MODES
+def test_paper_dark_spot_n200_nz512(mode):
     """Sec. 5.1 at the paper's parameters: N = 200, Nz = 512, dxi = 0.0351 um, omega0 = 1.2566e19
     rad/s, a coherent square of Na = 57 pixels (Eq. Na: sqrt(2 pi Nz) = 56.7), R = the dark-spot
     distance (Eq. darkspot).  S against the discrete FP64 answer (the field is separable: a 1D
@@ -157,7 +166,7 @@ def test_paper_dark_spot_n200_nz512():
     i0 = N // 2 - Na // 2
     m1 = np.zeros(N)
     m1[i0:i0 + Na] = 1.0
-    c, pw = _paper_handle(N, Nz, dxi, lam)
+    c, pw = _paper_handle(N, Nz, dxi, lam, mode)
     c.source_gsm(1e3, 1e3, 1.0)  # coherence widths of a kilometre: a coherent source
     mt = torch.from_numpy(np.outer(m1, m1).astype(np.complex64)).cuda()
     c.source_mask(mt)
@@ -224,13 +233,14 @@ def test_paper_annulus_n200_nz512():
     assert np.abs(mr.real - mut).max() < 0.04
 
 
-def test_phase_screen_rows_n200_nz512():
+@MODES
+def test_phase_screen_rows_n200_nz512(mode):
     # the GSM x phase-screen source at the paper's padded size, three rows against the oracle's
     # pruned-transform probes; Hermiticity on sampled columns
     import torch
     N, Nz, z = 200, 512, 0.5
     m = WL.phase_screen(N, seed=WL.SEED, corr_px=3.0)
-    c, pw = _paper_handle(N, Nz, D, LAM)
+    c, pw = _paper_handle(N, Nz, D, LAM, mode)
     c.source_gsm(SS, SM, 1.0)
     mt = torch.from_numpy(WL.to_c64(m)).cuda()
     c.source_mask(mt)
