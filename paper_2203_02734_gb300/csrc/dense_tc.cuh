@@ -12,10 +12,15 @@
 // Q is split once per propagation by qsplit_kernel into a global buffer laid out chunk by chunk
 // in the canonical K-major layout (no swizzle): per chunk, split s and K-step ks, core matrices
 // [kb < 2][row group < 2Np / 8] of 8 rows x 16 bytes, so one chunk is 384 Np contiguous bytes and
-// arrives by bulk copies.  Two chunk buffers: the copy of chunk c + 1 overlaps the MMAs of
-// chunk c.  The A tile (24 KB) is rebuilt per chunk by all 256 threads (thread t: column t mod
-// 128, K-step t / 128) once the previous chunk's MMAs have read it; its global loads are issued
-// before that wait.
+// arrives by bulk copies into one of two chunk buffers.  The A tile (24 KB) of a chunk is built by
+// all 256 threads (thread t: column t mod 128, K-step t / 128), in one of ABUF tiles (two where
+// they fit, Np <= 224, so that the split of chunk c + 1 overlaps the MMAs of chunk c).
+//
+// Schedule per chunk c (thread 0 issues, all threads split): thread 0 waits for chunk c's B
+// buffer, issues its MMAs and commits them to mbarrier mdone[c & 1], then waits for chunk
+// c + 1 - ABUF (which frees the A tile of chunk c + 1 and the B buffer of chunk c - 1) and starts
+// the copy of chunk c + 1's B into that buffer.  Chunk c is the (c / 2)-th completion of
+// mdone[c & 1]; no barrier is ever two phases ahead of a wait on it.
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -33,7 +38,9 @@ __host__ __device__ constexpr int npad(int N) { return (N + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t chunk_bytes(int N) { return (size_t)384 * npad(N); }
 __host__ __device__ constexpr int nchunks(int N) { return npad(N) / 16; }
 constexpr uint32_t A_BYTES = 3 * 2 * 4096;  // 3 splits x 2 K-steps x (128 rows x 16 bf16)
-__host__ __device__ constexpr size_t smem_bytes(int N) { return A_BYTES + 2 * chunk_bytes(N) + 64; }
+__host__ __device__ constexpr size_t smem_bytes(int N, int abuf) { return abuf * A_BYTES + 2 * chunk_bytes(N) + 64; }
+constexpr size_t SMEM_MAX = 232448;  // per-CTA dynamic shared memory limit
+__host__ __device__ constexpr int a_buffers(int N) { return smem_bytes(N, 2) <= SMEM_MAX ? 2 : 1; }
 // Tensor-memory columns to allocate: a power of two >= 32 holding D's 2 Np columns.
 __host__ __device__ constexpr uint32_t tmem_cols(int N) {
   return 2 * npad(N) <= 32 ? 32 : 2 * npad(N) <= 64 ? 64 : 2 * npad(N) <= 128 ? 128 : 2 * npad(N) <= 256 ? 256 : 512;
@@ -106,19 +113,19 @@ __device__ __forceinline__ void tmem_ld16(float (&r)[16], uint32_t taddr) {
 }
 
 // One tile of 128 columns j per CTA (grid = ceil(N^3 / 128)), 256 threads; tmem_cols(N)
-// tensor-memory columns and 2 x chunk + 24 KB of shared memory (one CTA per SM at N = 200).  A bounded wait that gives up
-// sets *err; the tile's outputs are then not written.
-template <bool S_OUT>
+// tensor-memory columns and ABUF x 24 KB + 2 x chunk of shared memory (one CTA per SM at N = 200).
+// A bounded wait that gives up sets *err; the tile's outputs are then not written.
+template <bool S_OUT, int ABUF>
 __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const unsigned char* __restrict__ Q,
                                                          int* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int N = p.N, Np = npad(N), nch = nchunks(N);
   const uint32_t cb = (uint32_t)chunk_bytes(N);
-  unsigned char* As = sm;
-  unsigned char* Bs0 = sm + A_BYTES;
-  uint64_t* bfull = reinterpret_cast<uint64_t*>(sm + A_BYTES + 2 * cb);  // [2]
-  uint64_t* mdone = bfull + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  unsigned char* As0 = sm;
+  unsigned char* Bs0 = sm + ABUF * A_BYTES;
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(sm + ABUF * A_BYTES + 2 * cb);  // [2]
+  uint64_t* mdone = bfull + 2;                                                 // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 2);
   const int t = threadIdx.x, w = t >> 5, m = t & 127, ks = t >> 7;
   const long long L = p.L, ncols = p.ncols;
   const long long j = (long long)blockIdx.x * 128 + m;
@@ -126,9 +133,10 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
 
   if (w == 0) tc16::tmem_alloc(tslot, tmem_cols(N));
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[1])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mdone)));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone[b])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc16::fence_before_sync();
@@ -148,20 +156,17 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
     if (nch > 1) load_chunk(1);
   }
   bool ok = true;
+  int okv = 1;
   for (int c = 0; c < nch; ++c) {
-    // the thread's 8 inputs n = 16 c + 8 ks + i of column j, loaded before the wait below
+    // the thread's 8 inputs n = 16 c + 8 ks + i of column j, loaded before the barrier below
     float2 x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int n = 16 * c + 8 * ks + i;
       x[i] = (jb >= 0 && n < N) ? p.in[jb + (long long)n * L] : make_float2(0.f, 0.f);
     }
-    int okv = 1;
-    if (c > 0 && t == 0) {
-      okv = ok && tc16::mbar_wait(mdone, (uint32_t)((c - 1) & 1));  // chunk c-1 read A and its B buffer
-      if (okv && c + 1 < nch) load_chunk(c + 1);
-    }
-    ok = __syncthreads_and(okv) != 0 && ok;
+    ok = __syncthreads_and(okv) != 0;  // thread 0 has waited for the chunk that used this A tile
+    unsigned char* As = As0 + (c % ABUF) * A_BYTES;
     // split into three BF16 parts: row m, K-step ks, core matrices kb = 0, 1 (4 complex each)
 #pragma unroll
     for (int kb = 0; kb < 2; ++kb) {
@@ -186,8 +191,8 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
     tc16::fence_before_sync();
     __syncthreads();
     if (t == 0 && ok) {
-      ok = tc16::mbar_wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1));
-      if (ok) {
+      bool good = tc16::mbar_wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1));
+      if (good) {
         tc16::fence_after_sync();
         constexpr int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
         const uint64_t a0 = tc16::sdesc(smem_u32(As), 2048, 128);
@@ -204,14 +209,20 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
               mma_np(tmem + (uint32_t)(h * Np), ad, bd, id, (c | q | s2) ? 1u : 0u);
             }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(mdone))
+                         smem_u32(&mdone[c & 1]))
                      : "memory");
+        const int wc = c + 1 - ABUF;  // frees A tile (c + 1) mod ABUF and B buffer (c + 1) & 1
+        if (wc >= 0) good = tc16::mbar_wait(&mdone[wc & 1], (uint32_t)((wc >> 1) & 1));
+        if (good && c >= 1 && c + 1 < nch) load_chunk(c + 1);
       }
-      if (!ok) atomicExch(err, 1);
+      if (!good) {
+        atomicExch(err, 1);
+        ok = false;
+      }
     }
+    okv = ok ? 1 : 0;
   }
-  int okv = 1;
-  if (t == 0) okv = ok && tc16::mbar_wait(mdone, (uint32_t)((nch - 1) & 1));
+  if (t == 0 && ok) okv = tc16::mbar_wait(&mdone[(nch - 1) & 1], (uint32_t)(((nch - 1) >> 1) & 1)) ? 1 : 0;
   ok = __syncthreads_and(okv) != 0;
   tc16::fence_after_sync();
   if (ok) {

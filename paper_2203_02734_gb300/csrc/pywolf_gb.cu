@@ -466,12 +466,17 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   if (tc) {  // the split matrices of E (point 2) and conj(E) (point 1), then four tensor-core passes
     const size_t qb = (size_t)pw::dense_tc::nchunks(N) * pw::dense_tc::chunk_bytes(N);
     if (!h->qbuf && (e = cudaMalloc(&h->qbuf, 2 * qb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc of the split DFT matrices");
+    const int abuf = pw::dense_tc::a_buffers(N);
+    const size_t smem = pw::dense_tc::smem_bytes(N, abuf);
     static size_t smem_set = 0;
-    const size_t smem = pw::dense_tc::smem_bytes(N);
     if (smem > smem_set) {
-      if ((e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if ((e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem)) != cudaSuccess ||
-          (e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(pw::dense_tc::axis_tc_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem)) != cudaSuccess)
         return cuda_fail(e, "shared memory of the tensor-core contraction");
       smem_set = smem;
@@ -488,10 +493,17 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
       ax.out = pass % 2 == 0 ? Xf : Wf;
       ax.scale = pass == 3 ? (float)((d * d / lz) * (d * d / lz)) : 1.0f;
       const unsigned char* qm = q + (pass < 2 ? 0 : qb);
-      if (pass < 3)
-        pw::dense_tc::axis_tc_kernel<false><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
-      else
-        pw::dense_tc::axis_tc_kernel<true><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+      if (abuf == 2) {
+        if (pass < 3)
+          pw::dense_tc::axis_tc_kernel<false, 2><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+        else
+          pw::dense_tc::axis_tc_kernel<true, 2><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+      } else {
+        if (pass < 3)
+          pw::dense_tc::axis_tc_kernel<false, 1><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+        else
+          pw::dense_tc::axis_tc_kernel<true, 1><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
+      }
       if (pass == 1 && ev && (e = cudaEventRecord(ev[1], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
     }
   }

@@ -254,3 +254,22 @@ def test_phase_screen_rows_n200_nz512(mode):
     for r in range(len(rows)):
         assert rel(Wrows[r], ref[r]) < 1e-5
         assert np.linalg.norm(cols[r] - np.conj(Wrows[r])) < 1e-5 * np.linalg.norm(ref[r])
+
+
+def test_tensor_core_single_a_tile_n240():
+    # N = 240 (Np = 240): the tensor-core contraction's shared memory holds one A tile only
+    import torch
+    N, Nz, z = 240, 320, 0.4
+    m = WL.phase_screen(N, seed=WL.SEED + 2, corr_px=3.0)
+    c, pw = _paper_handle(N, Nz, D, LAM, 2)
+    c.source_gsm(SS, SM, 1.0)
+    mt = torch.from_numpy(WL.to_c64(m)).cuda()
+    c.source_mask(mt)
+    c.propagate_fresnel(z)
+    rows = [(120, 120), (101, 133)]
+    Wrows = [c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows]
+    pw.pw_csd_check(c.h)
+    c.close()
+    ref = O.propagate_rows_gsm_padded(m, N, D, LAM, z, SS, SM, 1.0, rows, Nz)
+    for r in range(len(rows)):
+        assert rel(Wrows[r], ref[r]) < 1e-5
