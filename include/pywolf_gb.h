@@ -206,6 +206,13 @@ pw_status pw_csd_get_padding(const pw_csd* h, int* Nz);
  * no effect.  A bounded device wait of a tensor-core kernel that gives up is reported by
  * pw_csd_check (PW_ETIMEOUT). */
 enum { PW_DFT_AUTO = 0, PW_DFT_FP32 = 1, PW_DFT_TC_BF16X3 = 2 };
+
+/* Failure-detection test hook (no counterpart in the paper): in the next dense propagation on the
+ * tensor cores, CTA 0 of the first contraction never starts the copy of operand chunk `chunk`
+ * (>= 1), so its bounded wait gives up after about a second; the kernel frees its tensor memory
+ * and returns, that propagation's results are invalid, and pw_csd_check reports PW_ETIMEOUT.
+ * 0 turns it off; it applies to one propagation.  No GPU fault is involved. */
+pw_status pw_csd_inject_stall(pw_csd* h, int chunk);
 pw_status pw_csd_set_dft_mode(pw_csd* h, int mode);
 pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode);
 

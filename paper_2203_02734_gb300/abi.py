@@ -35,6 +35,7 @@ SIGNATURES = {
     "pw_csd_enable_timing": (_i, [_vp, _i]),
     "pw_csd_set_dft_mode": (_i, [_vp, _i]),
     "pw_csd_set_padding": (_i, [_vp, _i]),
+    "pw_csd_inject_stall": (_i, [_vp, _i]),
     "pw_csd_get_padding": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_get_dft_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
@@ -136,6 +137,10 @@ def pw_csd_reset(h, dxi_m):
 
 PW_DFT_AUTO, PW_DFT_FP32, PW_DFT_TC_BF16X3 = 0, 1, 2
 PW_MAX_N = 512
+
+
+def pw_csd_inject_stall(h, chunk):
+    _check(LIB.pw_csd_inject_stall(h, chunk))
 
 
 def pw_csd_set_padding(h, Nz):

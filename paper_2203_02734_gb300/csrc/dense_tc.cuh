@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   const uint32_t tmem = *tslot;
   const uint32_t id = idesc(Np);
   auto load_chunk = [&](int c) {  // one thread
+    if (p.stall > 0 && c == p.stall && blockIdx.x == 0) return;  // injected: this phase never completes
     unsigned char* dst = Bs0 + (c & 1) * cb;
     const unsigned char* src = Q + (size_t)c * cb;
     mbar_expect_tx(&bfull[c & 1], cb);
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   }
   bool ok = true;
   int okv = 1;
+  int committed = -1;  // thread 0: the last chunk whose MMAs were committed
   for (int c = 0; c < nch; ++c) {
     // the thread's 8 inputs n = 16 c + 8 ks + i of column j, loaded before the barrier below
     float2 x[8];
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mdone[c & 1]))
                      : "memory");
+        committed = c;
         const int wc = c + 1 - ABUF;  // frees A tile (c + 1) mod ABUF and B buffer (c + 1) & 1
         if (wc >= 0) good = tc16::mbar_wait(&mdone[wc & 1], (uint32_t)((wc >> 1) & 1));
         if (good && c >= 1 && c + 1 < nch) load_chunk(c + 1);
@@ -247,6 +250,8 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
     }
   } else if (t == 0) {
     atomicExch(err, 1);
+    // no MMA may still write tensor memory when it is freed (bounded, as every wait)
+    if (committed >= 0) tc16::mbar_wait(&mdone[committed & 1], (uint32_t)((committed >> 1) & 1));
   }
   tc16::fence_before_sync();
   __syncthreads();

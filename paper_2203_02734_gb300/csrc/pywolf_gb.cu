@@ -84,6 +84,7 @@ struct pw_csd {
   int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
   void* qbuf;        // split DFT matrices of the tensor-core dense path (allocated on first use)
+  int stall;         // failure-detection test: chunk whose copy CTA 0 leaves out, next dense TC run only
   // optional per-pass timing: 3 events per recorded propagation
   std::vector<cudaEvent_t> events;
   int timed;
@@ -487,12 +488,15 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
       pw::dense_tc::qsplit_kernel<<<num_sms() * 4, 256, 0, h->stream>>>(qa);
     }
     const dim3 tgrid((unsigned)((ax.ncols + 127) / 128));
+    ax.stall = h->stall;  // first contraction only, then cleared
+    h->stall = 0;
     for (int pass = 0; pass < 4; ++pass) {
       ax.L = L[pass];
       ax.in = pass % 2 == 0 ? Wf : Xf;
       ax.out = pass % 2 == 0 ? Xf : Wf;
       ax.scale = pass == 3 ? (float)((d * d / lz) * (d * d / lz)) : 1.0f;
       const unsigned char* qm = q + (pass < 2 ? 0 : qb);
+      if (pass > 0) ax.stall = 0;
       if (abuf == 2) {
         if (pass < 3)
           pw::dense_tc::axis_tc_kernel<false, 2><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
@@ -861,6 +865,14 @@ pw_status pw_csd_get_padding(const pw_csd* h, int* Nz) {
   g_err.clear();
   if (!h || !Nz) return fail(PW_EINVAL, "null argument");
   *Nz = h->Nz > 0 ? h->Nz : h->N;
+  return PW_OK;
+}
+
+pw_status pw_csd_inject_stall(pw_csd* h, int chunk) {
+  g_err.clear();
+  if (!h) return fail(PW_EINVAL, "null handle");
+  if (chunk < 0) return fail(PW_EINVAL, "chunk must be >= 0");
+  h->stall = chunk;
   return PW_OK;
 }
 

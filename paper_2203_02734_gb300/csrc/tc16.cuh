@@ -68,14 +68,24 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar) {
 __device__ __forceinline__ void mbar_inval(uint64_t* mbar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
-// Bounded wait for the completion of phase `parity`; false when it gave up.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the completion of phase `parity`: gives up (false) after about a second of
+// wall-clock time (or 2^24 polls), so that a phase that never completes ends the kernel with an
+// error flag instead of a hang.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
     asm volatile("{.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;}"
                  : "=r"(done)
                  : "r"(smem_u32(mbar)), "r"(parity)
                  : "memory");
+    if (!done && (it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
+  }
   return done != 0;
 }
 

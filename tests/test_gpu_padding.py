@@ -273,3 +273,27 @@ def test_tensor_core_single_a_tile_n240():
     ref = O.propagate_rows_gsm_padded(m, N, D, LAM, z, SS, SM, 1.0, rows, Nz)
     for r in range(len(rows)):
         assert rel(Wrows[r], ref[r]) < 1e-5
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recovers():
+    # failure detection without a GPU fault: CTA 0 never copies operand chunk 1, its bounded wait
+    # gives up (~1 s), pw_csd_check reports PW_ETIMEOUT, and the next propagation is right
+    import paper_2203_02734_gb300 as pw
+    N, Nz, z = 40, 64, 0.4  # Np = 48: three operand chunks
+    c = pw.CSD(N, D, LAM)
+    pw.pw_csd_set_padding(c.h, Nz)
+    pw.pw_csd_set_dft_mode(c.h, pw.PW_DFT_TC_BF16X3)
+    c.source_gsm(SS, SM, 1.0)
+    pw.pw_csd_inject_stall(c.h, 1)
+    c.propagate_fresnel(z)
+    with pytest.raises(pw.PwError, match="PW_ETIMEOUT"):
+        pw.pw_csd_check(c.h)
+    pw.pw_csd_check(c.h)  # the condition was cleared
+    pw.pw_csd_reset(c.h, D)
+    c.source_gsm(SS, SM, 1.0)
+    c.propagate_fresnel(z)
+    pw.pw_csd_check(c.h)
+    W = c.W.cpu().numpy().astype(np.complex128)
+    c.close()
+    Wr, _ = O.propagate_padded(O.gsm_source(N, D, SS, SM), D, LAM, z, Nz)
+    assert rel(W, Wr) < 1e-5
