@@ -38,7 +38,8 @@ WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
              WL.PHASE_SCREEN_N256["name"]: WL.PHASE_SCREEN_N256,
              WL.POLYCHROMATIC_BATCH["name"]: WL.POLYCHROMATIC_BATCH,
              WL.INVERSE_N96["name"]: WL.INVERSE_N96,
-             WL.PADDED_PHASE_SCREEN_N200["name"]: WL.PADDED_PHASE_SCREEN_N200}
+             WL.PADDED_PHASE_SCREEN_N200["name"]: WL.PADDED_PHASE_SCREEN_N200,
+             WL.PADDED_PHASE_SCREEN_N80["name"]: WL.PADDED_PHASE_SCREEN_N80}
 DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
 CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"

@@ -16,11 +16,8 @@
 // all 256 threads (thread t: column t mod 128, K-step t / 128), in one of ABUF tiles (two where
 // they fit, Np <= 224, so that the split of chunk c + 1 overlaps the MMAs of chunk c).
 //
-// Schedule per chunk c (thread 0 issues, all threads split): thread 0 waits for chunk c's B
-// buffer, issues its MMAs and commits them to mbarrier mdone[c & 1], then waits for chunk
-// c + 1 - ABUF (which frees the A tile of chunk c + 1 and the B buffer of chunk c - 1) and starts
-// the copy of chunk c + 1's B into that buffer.  Chunk c is the (c / 2)-th completion of
-// mdone[c & 1]; no barrier is ever two phases ahead of a wait on it.
+// Roles: eight warps split the operand chunks into A tiles and read the result back; one warp
+// copies B and issues the MMAs (see axis_tc_kernel for the mbarrier hand-offs).
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -31,14 +28,14 @@
 namespace pw {
 namespace dense_tc {
 
-constexpr int NT = 256;
+constexpr int NT = 288;  // 8 converter warps + 1 issuer warp
 constexpr int MAX_N = 256;
 
 __host__ __device__ constexpr int npad(int N) { return (N + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t chunk_bytes(int N) { return (size_t)384 * npad(N); }
 __host__ __device__ constexpr int nchunks(int N) { return npad(N) / 16; }
 constexpr uint32_t A_BYTES = 3 * 2 * 4096;  // 3 splits x 2 K-steps x (128 rows x 16 bf16)
-__host__ __device__ constexpr size_t smem_bytes(int N, int abuf) { return abuf * A_BYTES + 2 * chunk_bytes(N) + 64; }
+__host__ __device__ constexpr size_t smem_bytes(int N, int abuf) { return abuf * A_BYTES + 2 * chunk_bytes(N) + 128; }
 constexpr size_t SMEM_MAX = 232448;  // per-CTA dynamic shared memory limit
 __host__ __device__ constexpr int a_buffers(int N) { return smem_bytes(N, 2) <= SMEM_MAX ? 2 : 1; }
 // Tensor-memory columns to allocate: a power of two >= 32 holding D's 2 Np columns.
@@ -112,9 +109,16 @@ __device__ __forceinline__ void tmem_ld16(float (&r)[16], uint32_t taddr) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One tile of 128 columns j per CTA (grid = ceil(N^3 / 128)), 256 threads; tmem_cols(N)
-// tensor-memory columns and ABUF x 24 KB + 2 x chunk of shared memory (one CTA per SM at N = 200).
-// A bounded wait that gives up sets *err; the tile's outputs are then not written.
+// One tile of 128 columns j per CTA (grid = ceil(N^3 / 128)), NT = 288 threads: warps 0-7 split
+// the operand (thread t < 256: column t mod 128, K-step t / 128) and read the result back, warp 8
+// (one lane) copies B and issues the MMAs.  No block-wide barrier inside the chunk loop: the roles
+// hand off through mbarriers -- afull[b] (8 warp arrivals: A tile b is written), bfull[b] (bytes
+// of B buffer b have landed), mdone[b] (tcgen05.commit: the MMAs of the last chunk with parity b
+// have completed, so its A tile and B buffer are free).  A tile c mod ABUF holds chunk c, its
+// (c / ABUF)-th fill; no barrier can run two phases ahead of a wait on it (each next fill depends
+// on the completion being waited for).  Every wait is bounded; a wait that gives up sets the
+// shared abort flag and *err, after which no role waits again, and the tile's outputs are not
+// written.
 template <bool S_OUT, int ABUF>
 __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const unsigned char* __restrict__ Q,
                                                          int* err) {
@@ -125,81 +129,64 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   unsigned char* Bs0 = sm + ABUF * A_BYTES;
   uint64_t* bfull = reinterpret_cast<uint64_t*>(sm + ABUF * A_BYTES + 2 * cb);  // [2]
   uint64_t* mdone = bfull + 2;                                                 // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 2);
-  const int t = threadIdx.x, w = t >> 5, m = t & 127, ks = t >> 7;
+  uint64_t* afull = bfull + 4;                                                 // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bfull + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* committed = abort_flag + 1;  // the last chunk whose MMAs the issuer committed
+  const int t = threadIdx.x, w = t >> 5, m = t & 127, ks = (t >> 7) & 1;
   const long long L = p.L, ncols = p.ncols;
   const long long j = (long long)blockIdx.x * 128 + m;
-  const long long jb = j < ncols ? dense::col_base(j, L, N) : -1;
+  const long long jb = (t < 256 && j < ncols) ? dense::col_base(j, L, N) : -1;
 
   if (w == 0) tc16::tmem_alloc(tslot, tmem_cols(N));
   if (t == 0) {
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[b])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&afull[b])));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_flag = 0;
+    *committed = -1;
   }
   tc16::fence_before_sync();
   __syncthreads();
   tc16::fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t id = idesc(Np);
-  auto load_chunk = [&](int c) {  // one thread
-    if (p.stall > 0 && c == p.stall && blockIdx.x == 0) return;  // injected: this phase never completes
-    unsigned char* dst = Bs0 + (c & 1) * cb;
-    const unsigned char* src = Q + (size_t)c * cb;
-    mbar_expect_tx(&bfull[c & 1], cb);
-    const uint32_t piece = cb / 4;  // 96 Np bytes, a multiple of 16
-    for (int q = 0; q < 4; ++q) bulk_g2s(dst + q * piece, src + (size_t)q * piece, piece, &bfull[c & 1]);
+  auto fail_now = [&]() {
+    *abort_flag = 1;
+    atomicExch(err, 1);
   };
-  if (t == 0) {
-    load_chunk(0);
-    if (nch > 1) load_chunk(1);
-  }
-  bool ok = true;
-  int okv = 1;
-  int committed = -1;  // thread 0: the last chunk whose MMAs were committed
-  for (int c = 0; c < nch; ++c) {
-    // the thread's 8 inputs n = 16 c + 8 ks + i of column j, loaded before the barrier below
-    float2 x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int n = 16 * c + 8 * ks + i;
-      x[i] = (jb >= 0 && n < N) ? p.in[jb + (long long)n * L] : make_float2(0.f, 0.f);
-    }
-    ok = __syncthreads_and(okv) != 0;  // thread 0 has waited for the chunk that used this A tile
-    unsigned char* As = As0 + (c % ABUF) * A_BYTES;
-    // split into three BF16 parts: row m, K-step ks, core matrices kb = 0, 1 (4 complex each)
-#pragma unroll
-    for (int kb = 0; kb < 2; ++kb) {
-      uint32_t wv[3][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 v = x[4 * kb + q];
-        const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.x, v.y);
-        const float rx = v.x - __low2float(h1), ry = v.y - __high2float(h1);
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(rx, ry);
-        const __nv_bfloat162 h3 = __floats2bfloat162_rn(rx - __low2float(h2), ry - __high2float(h2));
-        wv[0][q] = tc16::bf2_bits(h1);
-        wv[1][q] = tc16::bf2_bits(h2);
-        wv[2][q] = tc16::bf2_bits(h3);
-      }
-#pragma unroll
-      for (int sp = 0; sp < 3; ++sp)
-        *reinterpret_cast<uint4*>(As + sp * 8192 + ks * 4096 + (kb * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
-            make_uint4(wv[sp][0], wv[sp][1], wv[sp][2], wv[sp][3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc16::fence_before_sync();
-    __syncthreads();
-    if (t == 0 && ok) {
-      bool good = tc16::mbar_wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1));
-      if (good) {
+  // bounded wait that also gives up at once when another role has aborted
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (*abort_flag) return false;
+    if (tc16::mbar_wait(bar, parity)) return true;
+    fail_now();
+    return false;
+  };
+
+  if (w == 8) {
+    // ---- the issuer: B copies and MMAs, one lane
+    if ((t & 31) == 0) {
+      const uint32_t id = idesc(Np);
+      auto load_chunk = [&](int c) {
+        if (p.stall > 0 && c == p.stall && blockIdx.x == 0) return;  // injected: this phase never completes
+        unsigned char* dst = Bs0 + (c & 1) * cb;
+        const unsigned char* src = Q + (size_t)c * cb;
+        mbar_expect_tx(&bfull[c & 1], cb);
+        const uint32_t piece = cb / 4;  // 96 Np bytes, a multiple of 16
+        for (int q = 0; q < 4; ++q) bulk_g2s(dst + q * piece, src + (size_t)q * piece, piece, &bfull[c & 1]);
+      };
+      load_chunk(0);
+      if (nch > 1) load_chunk(1);
+      constexpr int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
+      const uint32_t blk = (uint32_t)(64 * Np);
+      for (int c = 0; c < nch; ++c) {
+        if (!wait(&afull[c % ABUF], (uint32_t)((c / ABUF) & 1))) break;
+        if (!wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1))) break;
         tc16::fence_after_sync();
-        constexpr int ti[6] = {0, 0, 1, 0, 1, 2}, tj[6] = {0, 1, 0, 2, 1, 0};
-        const uint64_t a0 = tc16::sdesc(smem_u32(As), 2048, 128);
+        const uint64_t a0 = tc16::sdesc(smem_u32(As0 + (c % ABUF) * A_BYTES), 2048, 128);
         const uint64_t b0 = tc16::sdesc(smem_u32(Bs0 + (c & 1) * cb), (uint32_t)(32 * Np), 128);
-        const uint32_t blk = (uint32_t)(64 * Np);
 #pragma unroll
         for (int q = 0; q < 6; ++q)
 #pragma unroll
@@ -213,48 +200,91 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mdone[c & 1]))
                      : "memory");
-        committed = c;
-        const int wc = c + 1 - ABUF;  // frees A tile (c + 1) mod ABUF and B buffer (c + 1) & 1
-        if (wc >= 0) good = tc16::mbar_wait(&mdone[wc & 1], (uint32_t)((wc >> 1) & 1));
-        if (good && c >= 1 && c + 1 < nch) load_chunk(c + 1);
-      }
-      if (!good) {
-        atomicExch(err, 1);
-        ok = false;
+        *committed = c;
+        // B buffer (c + 1) & 1 last held chunk c - 1: refill it once those MMAs are done
+        if (c >= 1 && c + 1 < nch) {
+          if (!wait(&mdone[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1))) break;
+          load_chunk(c + 1);
+        }
       }
     }
-    okv = ok ? 1 : 0;
-  }
-  if (t == 0 && ok) okv = tc16::mbar_wait(&mdone[(nch - 1) & 1], (uint32_t)(((nch - 1) >> 1) & 1)) ? 1 : 0;
-  ok = __syncthreads_and(okv) != 0;
-  tc16::fence_after_sync();
-  if (ok) {
-    // warp w reads lanes 32 (w mod 4) .. + 31 (columns j) of output half w / 4
-    const int h = w >> 2;
-    const long long NN = (long long)N * N;
-    for (int q = 0; q < Np / 16; ++q) {  // 16 columns (8 complex outputs) per load, Np per half
-      float r[16];
-      tmem_ld16(r, tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(h * Np + 16 * q));
+  } else {
+    // ---- the converters: split the operand chunk by chunk, then read the result back
+    for (int c = 0; c < nch; ++c) {
+      float2 x[8];  // the thread's 8 inputs n = 16 c + 8 ks + i of column j
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int k = (h * Np + 16 * q) / 2 + i;
-        if (jb >= 0 && k < N) {
-          const float2 v = make_float2(r[2 * i] * p.scale, r[2 * i + 1] * p.scale);
-          p.out[jb + (long long)k * L] = v;
-          if (S_OUT) {
-            const int b = (int)(j / NN), cc = (int)((j / N) % N), d = (int)(j % N);
-            if (cc == k && d == b) p.S[k * N + b] = v.x;
+        const int n = 16 * c + 8 * ks + i;
+        x[i] = (jb >= 0 && n < N) ? p.in[jb + (long long)n * L] : make_float2(0.f, 0.f);
+      }
+      if (c >= ABUF) {  // A tile c mod ABUF last held chunk c - ABUF
+        const int pc = c - ABUF;
+        bool ok = true;
+        if ((t & 31) == 0) ok = wait(&mdone[pc & 1], (uint32_t)((pc >> 1) & 1));
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+      }
+      unsigned char* As = As0 + (c % ABUF) * A_BYTES;
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
+        uint32_t wv[3][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 v = x[4 * kb + q];
+          const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.x, v.y);
+          const float rx = v.x - __low2float(h1), ry = v.y - __high2float(h1);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(rx, ry);
+          const __nv_bfloat162 h3 = __floats2bfloat162_rn(rx - __low2float(h2), ry - __high2float(h2));
+          wv[0][q] = tc16::bf2_bits(h1);
+          wv[1][q] = tc16::bf2_bits(h2);
+          wv[2][q] = tc16::bf2_bits(h3);
+        }
+#pragma unroll
+        for (int sp = 0; sp < 3; ++sp)
+          *reinterpret_cast<uint4*>(As + sp * 8192 + ks * 4096 + (kb * 16 + (m >> 3)) * 128 + (m & 7) * 16) =
+              make_uint4(wv[sp][0], wv[sp][1], wv[sp][2], wv[sp][3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if ((t & 31) == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&afull[c % ABUF])) : "memory");
+    }
+    // the last chunk's MMAs complete after all earlier ones
+    bool ok = true;
+    if ((t & 31) == 0) ok = wait(&mdone[(nch - 1) & 1], (uint32_t)(((nch - 1) >> 1) & 1));
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    tc16::fence_after_sync();
+    if (ok && !*abort_flag) {
+      // warp w reads lanes 32 (w mod 4) .. + 31 (columns j) of output half w / 4
+      const int h = w >> 2;
+      const long long NN = (long long)N * N;
+      for (int q = 0; q < Np / 16; ++q) {  // 16 columns (8 complex outputs) per load, Np per half
+        float r[16];
+        tmem_ld16(r, tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(h * Np + 16 * q));
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = (h * Np + 16 * q) / 2 + i;
+          if (jb >= 0 && k < N) {
+            const float2 v = make_float2(r[2 * i] * p.scale, r[2 * i + 1] * p.scale);
+            p.out[jb + (long long)k * L] = v;
+            if (S_OUT) {
+              const int b = (int)(j / NN), cc = (int)((j / N) % N), d = (int)(j % N);
+              if (cc == k && d == b) p.S[k * N + b] = v.x;
+            }
           }
         }
       }
     }
-  } else if (t == 0) {
-    atomicExch(err, 1);
-    // no MMA may still write tensor memory when it is freed (bounded, as every wait)
-    if (committed >= 0) tc16::mbar_wait(&mdone[committed & 1], (uint32_t)((committed >> 1) & 1));
   }
   tc16::fence_before_sync();
   __syncthreads();
+  if (w == 8 && (t & 31) == 0 && *abort_flag && *committed >= 0) {
+    // no MMA may still write tensor memory when it is freed: the last commit covers all (bounded)
+    const int lc = *committed;
+    tc16::mbar_wait(&mdone[lc & 1], (uint32_t)((lc >> 1) & 1));
+  }
+  __syncthreads();
+  tc16::fence_after_sync();
   if (w == 0) tc16::tmem_dealloc(tmem, tmem_cols(N));
 }
 

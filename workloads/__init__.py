@@ -37,6 +37,10 @@ PHASE_SCREEN_N256 = dict(name="phase_screen_gsm_n256", N=256, dxi=20e-6, lam=633
 PADDED_PHASE_SCREEN_N200 = dict(name="padded_phase_screen_gsm_n200", N=200, Nz=512, dxi=20e-6,
                                 lam=633e-9, sigma_S=0.1e-3, sigma_mu=0.05e-3, A=1.0, z=0.5,
                                 corr_px=3.0, P1=(100, 100), sample_N=24, sample_Nz=62)
+# The padded workload scaled to a size a full profiler capture can take (N^4 complex64 = 0.33 GB,
+# above the L2 size; the same padding ratio 2.5).
+PADDED_PHASE_SCREEN_N80 = dict(PADDED_PHASE_SCREEN_N200, name="padded_phase_screen_gsm_n80", N=80, Nz=200,
+                               P1=(40, 40), sample_N=24, sample_Nz=60)
 INVERSE_N96 = dict(name="amplitude_mask_gsm_n96", N=96, dxi=20e-6, lam=633e-9, sigma_S=0.1e-3,
                    sigma_mu=0.05e-3, A=1.0, z=1.0, P1=(48, 48))
 
