@@ -128,7 +128,8 @@ pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask);
  * previous run or built by the user).  dev_W0 (N^4 complex64, device) may be dev_W itself.
  * hermitian != 0 declares W0(xi2, xi1) = conj W0(xi1, xi2) (true of every CSD, Sec. 3.3), which
  * lets the second pass store its output rows contiguously; hermitian == 0 selects the
- * general (strided-store) second pass.  Read during the next propagation. */
+ * general (strided-store) second pass for N <= 128, the four streaming passes at N = 256, and the
+ * dense path needs no declaration.  Read during the next propagation. */
 pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian);
 
 /* Delta-correlated (spatially incoherent) source W0 = weight d(xi1) delta(xi1 - xi2) with real

@@ -1,4 +1,4 @@
-"""N = 256 (the slice is distributed over a cluster of CTAs): the phase-screen GSM workload
+"""N = 256 (four streaming passes; the cluster engine in the tensor-core comparison mode): the phase-screen GSM workload
 (N = 256, dxi = 20 um, lambda = 633 nm, z = 0.5 m, unit-modulus screen with 3 px correlation)
 against the oracle's row probes, plus Hermiticity, power and trace conservation (GPU); and the
 same workload with the first radix-16 stage on the tensor cores (split-BF16x3), whose FP64
@@ -61,14 +61,31 @@ def test_phase_screen_n256():
         assert abs(S[a, b] - probe[r][a, b].real) < 1e-5 * np.abs(probe[0]).max()
 
 
-def test_n256_rejects_general_array():
+def test_n256_general_array():
+    # a non-Hermitian uploaded CSDA, W0 = u(xi1) v(xi2) (built on the device), two rows against the
+    # oracle's row route (Eq. W_fresnel, point-1 sum written out)
     import torch
     import paper_2203_02734_gb300 as pw
-    c = pw.CSD(256, 20e-6, 633e-9)
-    with pytest.raises(pw.PwError, match="PW_EUNSUPPORTED"):
-        pw.pw_source_array(c.h, c.W.data_ptr(), False)
-        pw.pw_propagate_fresnel(c.h, 0.5)
+    N, dxi, lam, z = 256, 20e-6, 633e-9, 0.5
+    u = WL.phase_screen(N, seed=WL.SEED + 5, corr_px=4.0)
+    x, _ = O.axis_coords(N, dxi)
+    env = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * (0.3e-3) ** 2))
+    u = (u * env).astype(np.complex64)
+    v = (WL.to_c64(WL.phase_screen(N, seed=WL.SEED + 6, corr_px=2.0)) * np.sqrt(env)).astype(np.complex64)
+    c = pw.CSD(N, dxi, lam)
+    ut, vt = torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()
+    for a in range(N):  # W0[a, b, :, :] = u[a, b] v
+        c.W[a].copy_(ut[a][:, None, None] * vt[None])
+    pw.pw_source_array(c.h, c.W.data_ptr(), False)
+    c.propagate_fresnel(z)
+    rows = [(128, 128), (121, 140)]
+    Wrows = [c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows]
+    pw.pw_csd_check(c.h)
     c.close()
+    u64, v64 = u.astype(np.complex128), v.astype(np.complex128)
+    ref = O.propagate_rows(lambda i1, j1: u64[i1, j1] * v64, N, dxi, lam, z, rows)
+    for r in range(len(rows)):
+        assert np.linalg.norm(Wrows[r] - ref[r]) / np.linalg.norm(ref[r]) < 1e-5
 
 
 def _sample_points(N, n, seed=7):
