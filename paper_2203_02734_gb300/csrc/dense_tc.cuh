@@ -168,7 +168,10 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   if (w == 8) {
     // ---- the issuer: B copies and MMAs, one lane
     if ((t & 31) == 0) {
-      const uint32_t id = idesc(Np);
+      // 2 Np output reals in one MMA where they fit its N (<= 256), else two halves of Np
+      const int halves = 2 * Np <= 256 ? 1 : 2;
+      const int nh = 2 * Np / halves;
+      const uint32_t id = idesc(nh);
       auto load_chunk = [&](int c) {
         if (p.stall > 0 && c == p.stall && blockIdx.x == 0) return;  // injected: this phase never completes
         unsigned char* dst = Bs0 + (c & 1) * cb;
@@ -192,10 +195,10 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
 #pragma unroll
           for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < halves; ++h) {
               const uint64_t ad = a0 + (uint64_t)((ti[q] * 8192 + s2 * 4096) >> 4);
-              const uint64_t bd = b0 + (uint64_t)(((tj[q] * 2 + s2) * blk + h * (Np / 8) * 128) >> 4);
-              mma_np(tmem + (uint32_t)(h * Np), ad, bd, id, (c | q | s2) ? 1u : 0u);
+              const uint64_t bd = b0 + (uint64_t)(((tj[q] * 2 + s2) * blk + h * (nh / 8) * 128) >> 4);
+              mma_np(tmem + (uint32_t)(h * nh), ad, bd, id, (c | q | s2) ? 1u : 0u);
             }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mdone[c & 1]))
