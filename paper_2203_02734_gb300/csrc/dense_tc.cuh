@@ -7,14 +7,15 @@
 //   D (128 x 2Np FP32, tensor memory lanes x columns): (Re C[k][j], Im C[k][j]) at 2k, 2k + 1;
 // Np = N rounded up to 16.  Both operands are split in three BF16 parts and D accumulates the six
 // products of tc16.cuh.  K runs in chunks of 16 complex inputs (32 reals, two MMA K-steps); the
-// output reals run in two halves of Np (the MMA's N <= 256), so a chunk is 6 x 2 x 2 = 24 MMAs.
+// 2 Np output reals go through one MMA where 2 Np <= 256 (the MMA's N limit), else through two
+// halves of Np, so a chunk is 6 x 2 = 12 or 6 x 2 x 2 = 24 MMAs.
 //
 // Q is split once per propagation by qsplit_kernel into a global buffer laid out chunk by chunk
 // in the canonical K-major layout (no swizzle): per chunk, split s and K-step ks, core matrices
 // [kb < 2][row group < 2Np / 8] of 8 rows x 16 bytes, so one chunk is 384 Np contiguous bytes and
 // arrives by bulk copies into one of two chunk buffers.  The A tile (24 KB) of a chunk is built by
-// all 256 threads (thread t: column t mod 128, K-step t / 128), in one of ABUF tiles (two where
-// they fit, Np <= 224, so that the split of chunk c + 1 overlaps the MMAs of chunk c).
+// the 256 converter threads (thread t: column t mod 128, K-step t / 128), in one of ABUF tiles
+// (two where they fit, Np <= 224, so that the split of chunk c + 1 overlaps the MMAs of chunk c).
 //
 // Roles: eight warps split the operand chunks into A tiles and read the result back; one warp
 // copies B and issues the MMAs (see axis_tc_kernel for the mbarrier hand-offs).
@@ -43,9 +44,9 @@ __host__ __device__ constexpr uint32_t tmem_cols(int N) {
   return 2 * npad(N) <= 32 ? 32 : 2 * npad(N) <= 64 ? 64 : 2 * npad(N) <= 128 ? 128 : 2 * npad(N) <= 256 ? 256 : 512;
 }
 
-// Instruction descriptor: D FP32, A and B BF16, K-major, M = 128, N = Np.
-__host__ __device__ constexpr uint32_t idesc(int Np) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Np >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor: D FP32, A and B BF16, K-major, M = 128, N = n (a multiple of 16 <= 256).
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 // Split Q for chunk c: element (row r < 2Np, K index kk < 32 of the chunk) of split s goes to
