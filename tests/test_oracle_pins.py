@@ -403,3 +403,15 @@ def test_padded_rejects_bad_sizes():
     for Nz in (4, 9):
         with pytest.raises(ValueError):
             O.propagate_padded(W0, DXI, LAM, 0.5, Nz)
+
+
+def test_padded_rows_match_padded_route_far_field():
+    rng = np.random.default_rng(4)
+    N, Nz = 10, 26
+    m = np.exp(2j * np.pi * rng.random((N, N)))
+    W0 = O.apply_mask(O.gsm_source(N, DXI, 0.1e-3, 0.05e-3), m)
+    a, _ = O.propagate_padded(W0, DXI, LAM, 2.0, Nz, farfield=True)
+    rows = [(5, 5), (2, 8)]
+    r = O.propagate_rows_gsm_padded(m, N, DXI, LAM, 2.0, 0.1e-3, 0.05e-3, 1.0, rows, Nz, farfield=True)
+    for k, (i, j) in enumerate(rows):
+        assert np.linalg.norm(r[k] - a[i, j]) / np.linalg.norm(a[i, j]) < 1e-12

@@ -39,3 +39,21 @@ def test_plain_fp32_matches_oracle(N):
 def test_plain_fp32_rejects_odd_n():
     with pytest.raises(ValueError):
         P.propagate_gsm_fp32(15, 1e-5, 6e-7, 0.3, 1e-4, 5e-5)
+
+
+def test_plain_fp32_padded_matches_padded_oracle():
+    # the padded workload's CPU leg: the source on the Nz grid (zeros around it), FFTs at Nz, the
+    # central N^4 block
+    pytest.importorskip("scipy.fft")
+    N, Nz, z = 12, 30, 0.5
+    m = WL.phase_screen(N, seed=WL.SEED, corr_px=3.0)
+    o = (Nz - N) // 2
+    mp = np.zeros((Nz, Nz), dtype=np.complex128)
+    mp[o:o + N, o:o + N] = m
+    W, S, mu, dx = P.propagate_gsm_fp32(Nz, CFG["dxi"], CFG["lam"], z, CFG["sigma_S"], CFG["sigma_mu"], 1.0,
+                                        mask=mp, workers=2)
+    Wc = W[o:o + N, o:o + N, o:o + N, o:o + N]
+    W0 = O.apply_mask(O.gsm_source(N, CFG["dxi"], CFG["sigma_S"], CFG["sigma_mu"]), m)
+    Wr, dxr = O.propagate_padded(W0, CFG["dxi"], CFG["lam"], z, Nz)
+    assert dx == pytest.approx(dxr, rel=1e-15)
+    assert _rel(Wc, Wr) < 1e-5
