@@ -2,14 +2,17 @@
 """Throughput of the propagation of a 4D cross-spectral density on GB300.
 
 Metric: 4D CSD points propagated per second (N^4 / time of one full propagation step) and the
-HBM-roofline fraction of the dominant kernel.  One step = reset to the source plane, GSM x
-circular aperture x thin lens source, Fresnel propagation (pass A: source build + input
-propagators + point-2 2D DFT; pass B: point-1 2D DFT + output propagators + S), then S and
-mu(P1, .) of the output plane.  Workload: N = 128 (268 M points, complex64 CSDA of 2.1 GB),
-dxi = 20 um, lambda = 633 nm, sigma_S = 0.1 mm, sigma_mu = 0.05 mm, aperture radius 0.8 mm,
-lens f = 0.3 m, z = 0.3 m.
+HBM-roofline fraction of the dominant kernel.  One step = reset to the source plane, the source
+(GSM x mask), Fresnel propagation (pass A: source build + input propagators + point-2 2D DFT;
+pass B: point-1 2D DFT + output propagators + S), then S and mu(P1, .) of the output plane.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Default workload (the headline line): N = 256 (4.3 G points, complex64 CSDA of 34 GB), GSM x a
+seeded unit-modulus phase screen (3 px correlation), dxi = 20 um, lambda = 633 nm, sigma_S =
+0.1 mm, sigma_mu = 0.05 mm, z = 0.5 m.  Inside the same line, under "n128": N = 128 (2.1 GB),
+GSM x 0.8 mm aperture x f = 0.3 m thin lens, z = 0.3 m.  Each is timed in blocks of --steps
+steps (CUDA events), repeated until the blocks span at least 0.5 s; the median block is reported.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 N > 1 runs under torch.distributed.run: each rank propagates its own copy of the workload
 (independent replicas, no collective on the data path), so the job processes N x N^4 points
@@ -40,7 +43,9 @@ WORKLOADS = {WL.GSM_APERTURE_LENS_N128["name"]: WL.GSM_APERTURE_LENS_N128,
              WL.INVERSE_N96["name"]: WL.INVERSE_N96,
              WL.PADDED_PHASE_SCREEN_N200["name"]: WL.PADDED_PHASE_SCREEN_N200,
              WL.PADDED_PHASE_SCREEN_N80["name"]: WL.PADDED_PHASE_SCREEN_N80}
-DEFAULT_WORKLOAD = WL.GSM_APERTURE_LENS_N128["name"]  # the workload the metric is quoted on
+# The headline: the largest single-GPU configuration (N = 256, 34 GB per CSDA); the N = 128
+# configuration is measured in the same run and reported inside the same line.
+DEFAULT_WORKLOAD = WL.PHASE_SCREEN_N256["name"]
 CFG = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "4D CSD points propagated/s (Fresnel, N^4) and % HBM roofline vs plain FP32 path"
 UNIT = "points/s"
@@ -50,11 +55,13 @@ SAMPLE_N = 64  # grid of the bounded CPU sample of the same configuration
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
-                   help="default: the N = 128 workload the metric is quoted on")
+                   help="default: the N = 256 phase-screen workload (with the N = 128 one inside its line)")
+    p.add_argument("--headline-only", action="store_true",
+                   help="with the default workload: skip the N = 128 measurement reported inside the line")
     p.add_argument("--dft", choices=["auto", "fp32", "tc_bf16x3"], default="auto",
                    help="arithmetic of the DFT work with a tensor-core form (the N = 256 first stage, the dense "
                         "contractions of padded workloads): auto (the library's per-path default), FP32 on the "
@@ -65,15 +72,16 @@ def parse_args():
     return a
 
 
-def source_mask_host(N):
+def source_mask_host(N, cfg=None):
     """Host-side (complex64) mask input of the workload: the aperture as a user mask for the N = 128
     workload, the seeded phase screen for the N = 256 one."""
     import numpy as np
-    if "corr_px" in CFG:
-        return WL.to_c64(WL.phase_screen(N, seed=WL.SEED, corr_px=CFG["corr_px"]))
+    cfg = cfg or CFG
+    if "corr_px" in cfg:
+        return WL.to_c64(WL.phase_screen(N, seed=WL.SEED, corr_px=cfg["corr_px"]))
     n = np.arange(N)
     r2 = (n[:, None] - N // 2) ** 2 + (N // 2 - n[None, :]) ** 2
-    rp = CFG["aperture"] / CFG["dxi"]
+    rp = cfg["aperture"] / cfg["dxi"]
     return (r2 <= rp * rp).astype(np.complex64)
 
 
@@ -335,89 +343,102 @@ class ClockSampler:
         return out
 
 
-def run_ours(args):
+def timed_blocks(run_block, stream, min_s=0.5, min_blocks=3, max_blocks=400):
+    """Run blocks of steps, each bracketed by CUDA events on `stream` (synchronised after each block),
+    until the blocks together span >= min_s seconds of device time and at least min_blocks ran.
+    Returns the device milliseconds of every block."""
+    import torch
+    ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while len(ms) < max_blocks and (len(ms) < min_blocks or sum(ms) < 1e3 * min_s):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run_block()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def measure(cfg, args, rank, world, dist):
+    """One workload of single propagations through the library: device-timed blocks of
+    `args.steps` steps, the per-pass times, the end-to-end blocks with host buffers, and the
+    roofline of the dominant pass.  Returns the fields of a bench line (rank 0) or None."""
     import torch
     import paper_2203_02734_gb300 as pw
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    N = CFG["N"]
+    N = cfg["N"]
     stream = torch.cuda.current_stream()
     W = torch.empty((N,) * 4, dtype=torch.complex64, device="cuda")
     work = torch.empty((N,) * 4, dtype=torch.complex64, device="cuda")
     S = torch.empty((N, N), dtype=torch.float32, device="cuda")
     mu = torch.empty((N, N), dtype=torch.complex64, device="cuda")
-    c = pw.CSD(N, CFG["dxi"], CFG["lam"], W=W, work=work, stream=stream)
+    c = pw.CSD(N, cfg["dxi"], cfg["lam"], W=W, work=work, stream=stream)
     h = c.h
-    P1 = CFG["P1"]
+    P1 = cfg["P1"]
     pw.pw_csd_set_dft_mode(h, {"auto": pw.PW_DFT_AUTO, "fp32": pw.PW_DFT_FP32,
                                "tc_bf16x3": pw.PW_DFT_TC_BF16X3}[args.dft])
-    if CFG.get("Nz"):
-        pw.pw_csd_set_padding(h, CFG["Nz"])
+    if cfg.get("Nz"):
+        pw.pw_csd_set_padding(h, cfg["Nz"])
 
-    screen = "corr_px" in CFG
-    mask_dev0 = torch.from_numpy(source_mask_host(N)).cuda() if screen else None
+    screen = "corr_px" in cfg
+    mask_dev0 = torch.from_numpy(source_mask_host(N, cfg)).cuda() if screen else None
 
     def step():
-        pw.pw_csd_reset(h, CFG["dxi"])
-        pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
+        pw.pw_csd_reset(h, cfg["dxi"])
+        pw.pw_source_gsm(h, cfg["sigma_S"], cfg["sigma_mu"], cfg["A"])
         if screen:
             pw.pw_source_mask(h, mask_dev0.data_ptr())
         else:
-            pw.pw_source_aperture(h, CFG["aperture"])
-            pw.pw_source_lens(h, CFG["lens_f"])
-        pw.pw_propagate_fresnel(h, CFG["z"])
+            pw.pw_source_aperture(h, cfg["aperture"])
+            pw.pw_source_lens(h, cfg["lens_f"])
+        pw.pw_propagate_fresnel(h, cfg["z"])
         pw.pw_spectral_density(h, S.data_ptr())
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
 
+    def block():
+        for _ in range(args.steps):
+            step()
+
     # tables, pass A, pass B, S kernel, mu kernel; padded: tables, dense tables, source, four
     # axis contractions (+ two matrix splits on the tensor cores), S kernel, mu kernel
-    launches_per_step = (11 if args.dft != "fp32" and N <= 256 else 9) if CFG.get("Nz") else 5
-    pw.pw_csd_enable_timing(h, max(args.steps, args.warmup, 1))
+    launches_per_step = (11 if args.dft != "fp32" and N <= 256 else 9) if cfg.get("Nz") else 5
+    max_blocks = 400
+    pw.pw_csd_enable_timing(h, max(args.steps * max_blocks, args.warmup, 1))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     pw.pw_csd_pass_times(h)  # discard warm-up records
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     clock = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
     t0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    blocks = timed_blocks(block, stream, max_blocks=max_blocks)
     t1 = time.time()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = statistics.median(blocks)
     ms_a, ms_b, nrec = pw.pw_csd_pass_times(h)
     clocks = clock.stop(t0, t1) if clock else None
     ms = max_over_ranks(ms, dist, "cuda")
 
-    # End to end through the public API with host buffers: each step copies the aperture,
-    # given as a user mask in pinned host memory, to the device and reads S and mu back into
-    # pinned host memory; the same configuration as above, so the result is identical.
-    mask_h = torch.from_numpy(source_mask_host(N)).pin_memory()
+    # End to end through the public API with host buffers: each step copies the source mask (the
+    # aperture as a user mask for the N = 128 workload, the phase screen for N = 256) from pinned
+    # host memory to the device and reads S and mu back into pinned host memory; the same
+    # configuration as above, so the result is identical.
+    mask_h = torch.from_numpy(source_mask_host(N, cfg)).pin_memory()
     mask_d = torch.empty_like(mask_h, device="cuda")
     S_h = torch.empty((N, N), dtype=torch.float32).pin_memory()
     mu_h = torch.empty((N, N), dtype=torch.complex64).pin_memory()
 
     def step_e2e():
         mask_d.copy_(mask_h, non_blocking=True)
-        pw.pw_csd_reset(h, CFG["dxi"])
-        pw.pw_source_gsm(h, CFG["sigma_S"], CFG["sigma_mu"], CFG["A"])
+        pw.pw_csd_reset(h, cfg["dxi"])
+        pw.pw_source_gsm(h, cfg["sigma_S"], cfg["sigma_mu"], cfg["A"])
         pw.pw_source_mask(h, mask_d.data_ptr())
         if not screen:
-            pw.pw_source_lens(h, CFG["lens_f"])
-        pw.pw_propagate_fresnel(h, CFG["z"])
+            pw.pw_source_lens(h, cfg["lens_f"])
+        pw.pw_propagate_fresnel(h, cfg["z"])
         pw.pw_spectral_density(h, S.data_ptr())
         pw.pw_degree_of_coherence(h, P1[0], P1[1], mu.data_ptr())
         S_h.copy_(S, non_blocking=True)
@@ -430,19 +451,21 @@ def run_ours(args):
     same = bool(torch.equal(S_h, S_ref.cpu()))
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    te0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
-    torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    te = max_over_ranks(te, dist, "cuda")
+    e2e_blocks = []
+    while len(e2e_blocks) < 3 or sum(e2e_blocks) < 0.5:
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        e2e_blocks.append(time.perf_counter() - te0)
+    te = max_over_ranks(statistics.median(e2e_blocks), dist, "cuda")
     pw.pw_csd_pass_times(h)
     c.close()
+    del W, work
+    torch.cuda.empty_cache()
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
+        return None
 
     pts = N ** 4
     value = job_throughput(world, pts, args.steps, ms / 1e3)
@@ -453,18 +476,18 @@ def run_ours(args):
     else:
         kern, avg, bytes_launch = "pass_a", avg_a, 8 * pts
     achieved = bytes_launch / (avg / 1e3) / 1e9
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": CFG["name"], "N": N, "dft_first_stage": args.dft, "points_per_step": pts,
-                   "dxi_m": CFG["dxi"],
-                   "lambda_m": CFG["lam"], "z_m": CFG["z"], "aperture_m": CFG.get("aperture"),
-                   "lens_f_m": CFG.get("lens_f"), "phase_screen_corr_px": CFG.get("corr_px"), "P1": list(P1),
+    return {
+        "value": value, "ms_per_step": ms / args.steps,
+        "config": {"workload": cfg["name"], "N": N, "dft_first_stage": args.dft, "points_per_step": pts,
+                   "dxi_m": cfg["dxi"],
+                   "lambda_m": cfg["lam"], "z_m": cfg["z"], "aperture_m": cfg.get("aperture"),
+                   "lens_f_m": cfg.get("lens_f"), "phase_screen_corr_px": cfg.get("corr_px"), "P1": list(P1),
                    "parallelism": "replicas x%d" % world,
                    "l2": "inputs larger than L2: 2 x %.1f GB CSDA buffers stream through HBM every step"
-                         % (8 * pts / 1e9)},
-        "roofline": roofline_dense(N, pts, avg_a, avg_b, clocks, args.dft != "fp32" and N <= 256) if CFG.get("Nz") else
+                         % (8 * pts / 1e9),
+                   "timing": "median of %d blocks of %d steps (%.2f s of device time in all)"
+                             % (len(blocks), args.steps, sum(blocks) / 1e3)},
+        "roofline": roofline_dense(N, pts, avg_a, avg_b, clocks, args.dft != "fp32" and N <= 256) if cfg.get("Nz") else
                     {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(kern, N),
                      "algorithmic_bytes_per_launch": bytes_launch,
@@ -474,10 +497,38 @@ def run_ours(args):
                 "h2d_bytes_per_step": mask_h.numel() * 8, "d2h_bytes_per_step": S_h.numel() * 4 + mu_h.numel() * 8,
                 "result_matches_device_path": same},
         "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
         "clocks": clocks,
     }
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # The headline workload (by default N = 256, the largest single-GPU configuration); with it, the
+    # N = 128 workload is measured the same way and reported inside the same line.
+    second = None
+    if CFG is WL.PHASE_SCREEN_N256 and not args.headline_only:
+        second = measure(WL.GSM_APERTURE_LENS_N128, args, rank, world, dist)
+    r = measure(CFG, args, rank, world, dist)
     if dist:
         dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    for k in ("config", "roofline", "e2e", "gpu_launches", "gpu_launches_per_step", "clocks"):
+        line[k] = r[k]
+    if second is not None:
+        line["n128"] = {k: second[k] for k in ("value", "ms_per_step", "config", "roofline", "e2e", "clocks")}
+        line["n128"]["unit"] = UNIT
     if world == 1:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_plain_fp32"] = cpu_plain_fp32()

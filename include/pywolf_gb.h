@@ -28,6 +28,9 @@
  *   only small O(N^2) tables (chirps, twiddles, GSM factors, S) per handle.
  * Streams: all device work is enqueued on the handle's stream and is asynchronous; results
  *   in device memory are valid once that stream has been synchronised.
+ * Alignment: dev_W and dev_work 16-byte aligned (bulk and tensor copies); complex64 arrays
+ *   (masks, uploaded CSDAs, mu) 8-byte aligned; float arrays 4-byte aligned.  A misaligned
+ *   pointer returns PW_EINVAL before any device work.
  * Errors: no call aborts, traps or prints.  Each returns a pw_status; the message of the
  *   last failure on the calling thread is returned by pw_last_error().  Invalid arguments
  *   are rejected on the host before any device work is enqueued.
@@ -210,9 +213,11 @@ enum { PW_DFT_AUTO = 0, PW_DFT_FP32 = 1, PW_DFT_TC_BF16X3 = 2 };
 
 /* Failure-detection test hook (no counterpart in the paper): in the next dense propagation on the
  * tensor cores, CTA 0 of the first contraction never starts the copy of operand chunk `chunk`
- * (>= 1), so its bounded wait gives up after about a second; the kernel frees its tensor memory
- * and returns, that propagation's results are invalid, and pw_csd_check reports PW_ETIMEOUT.
- * 0 turns it off; it applies to one propagation.  No GPU fault is involved. */
+ * (chunk >= 1), or its splitting warps never announce the A tile of chunk -chunk (chunk <= -1;
+ * the copy of that chunk's B operand is then already in flight).  The bounded wait gives up after
+ * about a second; the kernel waits (bounded) for its committed MMAs and its started copies, frees
+ * its tensor memory and returns; that propagation's results are invalid, and pw_csd_check reports
+ * PW_ETIMEOUT.  0 turns it off; it applies to one propagation.  No GPU fault is involved. */
 pw_status pw_csd_inject_stall(pw_csd* h, int chunk);
 pw_status pw_csd_set_dft_mode(pw_csd* h, int mode);
 pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode);
@@ -324,9 +329,11 @@ pw_status pw_batch_destroy(pw_batch* b);
  *   N, dxi_m, lambda_m, z_m, sigma_S_m, sigma_mu_m, amplitude  as for the handle calls
  *   aperture_m  radius of the inclusive circular aperture, <= 0 for none
  *   lens_f_m    focal length of the thin lens in the source plane, 0 for none
- *   dev_mask    N x N complex64 device mask applied as m*(xi1) W m(xi2), or NULL
- *   dev_W_out   device buffer of >= N^4 * 8 bytes (W_bytes) receiving the propagated CSDA
- *   dev_S_out   device buffer of N x N float32 receiving S of the output plane
+ *   dev_mask    N x N complex64 device mask applied as m*(xi1) W m(xi2), or NULL; 8-byte aligned
+ *   dev_W_out   device buffer of >= N^4 * 8 bytes (W_bytes) receiving the propagated CSDA;
+ *               16-byte aligned (it is written by bulk copies)
+ *   dev_S_out   device buffer of N x N float32 receiving S of the output plane; 4-byte aligned
+ * A misaligned pointer returns PW_EINVAL before anything is launched.
  *   stream      cudaStream_t (NULL = legacy default stream); work is asynchronous on it
  * The output sampling is lambda z / (N dxi).  The first call on a device looks up the
  * device address of the internal array (cudaGetSymbolAddress); make that first call before

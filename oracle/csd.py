@@ -33,7 +33,7 @@ __all__ = [
     "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
     "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
     "propagate_rows_gsm", "s_loss", "s_loss_gradient", "propagate_padded", "padded_dft_matrix",
-    "propagate_rows_gsm_padded",
+    "propagate_rows_gsm_padded", "axis_kernels", "bilinear_probes", "bilinear_probes_gsm",
 ]
 
 
@@ -268,6 +268,61 @@ def propagate_rows_gsm(m, N, dxi, lam, z, sigma_S, sigma_mu, A, rows, farfield=F
         out[r] = centred_dft2(inner, axes=(0, 1), sign=-1)
         out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
     return out
+
+
+def axis_kernels(N, dxi, lam, z, farfield=False):
+    """Per-axis factors of the kernel h(X, xi) of propagate_direct: h(X, xi) = Hx[i', i] Hy[j', j]
+    for the output point X = (X(i'), Y(j')) and the source point xi = (x(i), y(j)).
+    Fresnel: |X - xi|^2 splits into the two axes, Hx[i', i] = exp(i pi (X(i') - x(i))^2/(lambda z));
+    far field: q(X) exp(-2 pi i X.xi/(lambda z)) splits likewise (Eq. W_farfield)."""
+    x, y = axis_coords(N, dxi)
+    X, Y = axis_coords(N, output_sampling(N, dxi, lam, z))
+    lz = lam * z
+
+    def one(out, src):
+        if farfield:
+            return q(z, out ** 2, lam)[:, None] * np.exp(-2j * np.pi * out[:, None] * src[None, :] / lz)
+        return np.exp(1j * np.pi * (out[:, None] - src[None, :]) ** 2 / lz)
+    return one(X, x), one(Y, y)
+
+
+def _probe_vectors(U, V, N, dxi, lam, z, farfield):
+    """alpha_k(xi) = sum_X h(X, xi) u_k(X) and beta_k likewise for v_k (the kernel applied to the
+    probe fields, per axis: Hx^T u Hy)."""
+    Hx, Hy = axis_kernels(N, dxi, lam, z, farfield)
+    U = np.asarray(U, dtype=np.complex128).reshape(-1, N, N)
+    V = np.asarray(V, dtype=np.complex128).reshape(-1, N, N)
+    al = np.einsum("ai,kab,bj->kij", Hx, U, Hy)
+    be = np.einsum("ai,kab,bj->kij", Hx, V, Hy)
+    return al, be
+
+
+def bilinear_probes(W0, dxi, lam, z, U, V, farfield=False):
+    """Quadratic forms p_k = u_k^H W_B v_k = sum_{X1, X2} conj(u_k(X1)) W_B(X1, X2) v_k(X2) of the
+    propagated CSDA, from the source CSDA W0 without forming W_B: with W_B = s h* W0 h^T
+    (Eq. W_general on the grid, as in propagate_direct),
+      p_k = s sum_{xi1, xi2} conj(alpha_k(xi1)) W0(xi1, xi2) beta_k(xi2),
+      alpha_k(xi) = sum_X h(X, xi) u_k(X),  beta_k(xi) = sum_X h(X, xi) v_k(X).
+    U, V: (K, N, N) probe fields on the output grid.  O(N^4) per probe: small N."""
+    N = W0.shape[0]
+    al, be = _probe_vectors(U, V, N, dxi, lam, z, farfield)
+    Wf = np.asarray(W0, dtype=np.complex128).reshape(N * N, N * N)
+    s = propagation_scale(dxi, lam, z)
+    return np.array([s * (np.conj(al[k].ravel()) @ (Wf @ be[k].ravel())) for k in range(al.shape[0])])
+
+
+def bilinear_probes_gsm(m, N, dxi, lam, z, sigma_S, sigma_mu, A, U, V, farfield=False):
+    """bilinear_probes for the masked GSM source W0 = A m*(xi1) g(i1, i2) g(j1, j2) m(xi2) (Sec. 5.4,
+    reading R1; g the per-axis GSM factor, the same matrix on both axes because y(j) = -x(j)):
+    the source sum becomes sum_{i1, j1} conj(alpha m)(i1, j1) [g (m beta) g](i1, j1), O(N^3) per
+    probe, for large N."""
+    x, _ = axis_coords(N, dxi)
+    g = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * sigma_S ** 2)
+               - (x[:, None] - x[None, :]) ** 2 / (2 * sigma_mu ** 2))
+    m = np.asarray(m, dtype=np.complex128)
+    al, be = _probe_vectors(U, V, N, dxi, lam, z, farfield)
+    s = propagation_scale(dxi, lam, z)
+    return np.array([s * A * np.sum(np.conj(al[k] * m) * (g @ (m * be[k]) @ g)) for k in range(al.shape[0])])
 
 
 def _check_padding(N, Nz):

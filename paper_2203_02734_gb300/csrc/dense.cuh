@@ -95,7 +95,8 @@ struct AxisArgs {
   const float2* in;
   float2* out;
   float* S;
-  int stall;  // failure-detection test: CTA 0 of the tensor-core kernel never copies chunk `stall` (0 = off)
+  int stall;  // failure-detection test (0 = off): CTA 0 of the tensor-core kernel never copies operand chunk
+              // `stall` (> 0), or never announces A tile -stall (< 0)
 };
 
 constexpr int BM = 64, BN = 64, BK = 16, PITCH = 66, NT = 256;

@@ -134,6 +134,9 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bfull + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   volatile int* committed = abort_flag + 1;  // the last chunk whose MMAs the issuer committed
+  // Issuer lane only: chunks whose B copies were started (bit c) and whose bfull wait completed
+  // (bit c); on an abort, copies still in flight are drained before the CTA exits.
+  uint32_t b_issued = 0, b_landed = 0;
   const int t = threadIdx.x, w = t >> 5, m = t & 127, ks = (t >> 7) & 1;
   const long long L = p.L, ncols = p.ncols;
   const long long j = (long long)blockIdx.x * 128 + m;
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
       const uint32_t id = idesc(nh);
       auto load_chunk = [&](int c) {
         if (p.stall > 0 && c == p.stall && blockIdx.x == 0) return;  // injected: this phase never completes
+        b_issued |= 1u << c;
         unsigned char* dst = Bs0 + (c & 1) * cb;
         const unsigned char* src = Q + (size_t)c * cb;
         mbar_expect_tx(&bfull[c & 1], cb);
@@ -188,6 +192,7 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
       for (int c = 0; c < nch; ++c) {
         if (!wait(&afull[c % ABUF], (uint32_t)((c / ABUF) & 1))) break;
         if (!wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1))) break;
+        b_landed |= 1u << c;
         tc16::fence_after_sync();
         const uint64_t a0 = tc16::sdesc(smem_u32(As0 + (c % ABUF) * A_BYTES), 2048, 128);
         const uint64_t b0 = tc16::sdesc(smem_u32(Bs0 + (c & 1) * cb), (uint32_t)(32 * Np), 128);
@@ -250,7 +255,10 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if ((t & 31) == 0)
+      // injected (p.stall < 0): CTA 0 never announces A tile -p.stall, so the issuer's wait gives up
+      // while the B copy of that chunk may still be in flight
+      const bool skip = p.stall < 0 && c == -p.stall && blockIdx.x == 0;
+      if ((t & 31) == 0 && !skip)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&afull[c % ABUF])) : "memory");
     }
     // the last chunk's MMAs complete after all earlier ones
@@ -282,10 +290,16 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   }
   tc16::fence_before_sync();
   __syncthreads();
-  if (w == 8 && (t & 31) == 0 && *abort_flag && *committed >= 0) {
+  if (w == 8 && (t & 31) == 0 && *abort_flag) {
     // no MMA may still write tensor memory when it is freed: the last commit covers all (bounded)
-    const int lc = *committed;
-    tc16::mbar_wait(&mdone[lc & 1], (uint32_t)((lc >> 1) & 1));
+    if (*committed >= 0) {
+      const int lc = *committed;
+      tc16::mbar_wait(&mdone[lc & 1], (uint32_t)((lc >> 1) & 1));
+    }
+    // no bulk copy may still write shared memory when the CTA exits: wait (bounded) for every B
+    // copy that was started and not yet seen complete; at most one is outstanding per buffer
+    for (int c = 0; c < nch; ++c)
+      if ((b_issued >> c) & 1u && !((b_landed >> c) & 1u)) tc16::mbar_wait(&bfull[c & 1], (uint32_t)((c >> 1) & 1));
   }
   __syncthreads();
   tc16::fence_after_sync();

@@ -10,6 +10,8 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -73,27 +75,57 @@ pw_status scratch_address(void** out) {
   return PW_OK;
 }
 
+// Persistent grids of the two passes for N on the current device: occupancy queried on the
+// first call per (device, N) and kept, so later calls issue no attribute or occupancy queries.
 template <int N>
-cudaError_t run(const CUtensorMap& vmap, const pw::TableArgs& t, const pw::PassAArgs& a, const pw::PassBArgs& b,
-                cudaStream_t s) {
+pw_status pass_grids(int* ga, int* gb) {
+  static int grid_a[kMaxDevices], grid_b[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PW_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(PW_EUNSUPPORTED, "device ordinal %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (grid_a[dev] == 0) {
+    int sms = 0, per_a = 0, per_b = 0;
+    const int NN = N * N;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, pw::pass_a_kernel<N, pw::SRC_GSM>,
+                                                           pw::Plan<N>::NT, pw::pass_a_smem<N>())) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, pw::pass_b_kernel<N, pw::W_HERM>,
+                                                           pw::Plan<N>::NT, pw::pass_b_smem<N>())) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PW_ECUDA, "occupancy of the propagation passes: %s", cudaGetErrorString(e));
+    }
+    grid_a[dev] = (int)std::min<long>((long)std::max(per_a, 1) * std::max(sms, 1), NN);
+    grid_b[dev] = (int)std::min<long>((long)std::max(per_b, 1) * std::max(sms, 1), NN);
+  }
+  *ga = grid_a[dev];
+  *gb = grid_b[dev];
+  return PW_OK;
+}
+
+template <int N>
+pw_status run(const CUtensorMap& vmap, const pw::TableArgs& t, const pw::PassAArgs& a, const pw::PassBArgs& b,
+              cudaStream_t s) {
+  int ga = 0, gb = 0;
+  pw_status st = pass_grids<N>(&ga, &gb);
+  if (st != PW_OK) return st;
   const int NN = N * N;
   pw::tables_kernel<<<(NN + 255) / 256, 256, 0, s>>>(t);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per_a = 1, per_b = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, pw::pass_a_kernel<N, false>, pw::Plan<N>::NT,
-                                                pw::pass_a_smem<N>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, pw::pass_b_kernel<N, true>, pw::Plan<N>::NT,
-                                                pw::pass_b_smem<N>());
-  const int ga = (int)std::min<long>((long)std::max(per_a, 1) * std::max(sms, 1), NN);
-  const int gb = (int)std::min<long>((long)std::max(per_b, 1) * std::max(sms, 1), NN);
-  pw::pass_a_kernel<N, false><<<ga, pw::Plan<N>::NT, pw::pass_a_smem<N>(), s>>>(vmap, a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  pw::pass_b_kernel<N, true><<<gb, pw::Plan<N>::NT, pw::pass_b_smem<N>(), s>>>(b);
-  return cudaGetLastError();
+  if (e == cudaSuccess) {
+    pw::pass_a_kernel<N, pw::SRC_GSM><<<ga, pw::Plan<N>::NT, pw::pass_a_smem<N>(), s>>>(vmap, a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    pw::pass_b_kernel<N, pw::W_HERM><<<gb, pw::Plan<N>::NT, pw::pass_b_smem<N>(), s>>>(b);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PW_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  }
+  return PW_OK;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -129,6 +161,13 @@ extern "C" pw_status pw_propagate_gsm_fresnel_noalloc(int N, double dxi_m, doubl
     return fail(PW_EINVAL, "amplitude, aperture and focal length must be finite");
   if (!dev_W_out || !dev_S_out) return fail(PW_EINVAL, "dev_W_out and dev_S_out must be non-null");
   if (W_bytes < pw_csda_bytes(N)) return fail(PW_ESIZE, "dev_W_out needs %zu bytes (got %zu)", pw_csda_bytes(N), W_bytes);
+  // Pass B leaves W by bulk copies (16-byte aligned global addresses), S is written as floats and
+  // the mask is read as 8-byte complex values: misaligned pointers are refused before any launch.
+  if (reinterpret_cast<uintptr_t>(dev_W_out) % 16 != 0)
+    return fail(PW_EINVAL, "dev_W_out must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(dev_S_out) % 4 != 0) return fail(PW_EINVAL, "dev_S_out must be 4-byte aligned");
+  if (dev_mask && reinterpret_cast<uintptr_t>(dev_mask) % 8 != 0)
+    return fail(PW_EINVAL, "dev_mask must be 8-byte aligned");
 
   void* base = nullptr;
   pw_status st = scratch_address(&base);
@@ -195,21 +234,16 @@ extern "C" pw_status pw_propagate_gsm_fresnel_noalloc(int N, double dxi_m, doubl
   b.scale = (float)((d * d / lz) * (d * d / lz));
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaErrorInvalidValue;
   switch (N) {
-    case 2: e = run<2>(vmap, t, a, b, s); break;
-    case 4: e = run<4>(vmap, t, a, b, s); break;
-    case 6: e = run<6>(vmap, t, a, b, s); break;
-    case 8: e = run<8>(vmap, t, a, b, s); break;
-    case 12: e = run<12>(vmap, t, a, b, s); break;
-    case 16: e = run<16>(vmap, t, a, b, s); break;
-    case 24: e = run<24>(vmap, t, a, b, s); break;
-    case 32: e = run<32>(vmap, t, a, b, s); break;
+    case 2: return run<2>(vmap, t, a, b, s);
+    case 4: return run<4>(vmap, t, a, b, s);
+    case 6: return run<6>(vmap, t, a, b, s);
+    case 8: return run<8>(vmap, t, a, b, s);
+    case 12: return run<12>(vmap, t, a, b, s);
+    case 16: return run<16>(vmap, t, a, b, s);
+    case 24: return run<24>(vmap, t, a, b, s);
+    case 32: return run<32>(vmap, t, a, b, s);
     default: break;
   }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(PW_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
-  }
-  return PW_OK;
+  return fail(PW_EUNSUPPORTED, "no propagation plan for N = %d", N);
 }

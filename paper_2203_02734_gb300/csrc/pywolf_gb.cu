@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -41,6 +42,10 @@ pw_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Device pointers are dereferenced as 16-byte bulk / tensor copies (the CSDA buffers), 8-byte
+// complex values (masks, uploaded arrays, mu) or floats (S, diagonals).
+bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
 enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3, SRC_DIAGONAL = 4 };
 
@@ -774,6 +779,7 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
     const char* b0 = reinterpret_cast<const char*>(dev_work);
     if (a0 < b0 + need && b0 < a0 + need) return fail(PW_EINVAL, "dev_W and dev_work overlap");
   }
+  if (!aligned(dev_W, 16) || !aligned(dev_work, 16)) return fail(PW_EINVAL, "dev_W and dev_work must be 16-byte aligned");
   pw_csd* h = new pw_csd{};
   h->N = N;
   h->d = dxi_m;
@@ -933,7 +939,6 @@ pw_status pw_csd_get_padding(const pw_csd* h, int* Nz) {
 pw_status pw_csd_inject_stall(pw_csd* h, int chunk) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
-  if (chunk < 0) return fail(PW_EINVAL, "chunk must be >= 0");
   h->stall = chunk;
   return PW_OK;
 }
@@ -989,6 +994,7 @@ pw_status pw_source_lens(pw_csd* h, double focal_m) {
 pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
+  if (dev_mask && !aligned(dev_mask, 8)) return fail(PW_EINVAL, "dev_mask must be 8-byte aligned");
   h->mask = dev_mask;
   return PW_OK;
 }
@@ -997,6 +1003,7 @@ pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!dev_W0) return fail(PW_EINVAL, "dev_W0 is null");
+  if (!aligned(dev_W0, 8)) return fail(PW_EINVAL, "dev_W0 must be 8-byte aligned");
   {
     const size_t need = pw_csda_bytes(h->N);
     const char* a0 = reinterpret_cast<const char*>(dev_W0);
@@ -1014,6 +1021,7 @@ pw_status pw_source_diagonal(pw_csd* h, const float* dev_d, double weight) {
   g_err.clear();
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!dev_d) return fail(PW_EINVAL, "dev_d is null");
+  if (!aligned(dev_d, 4)) return fail(PW_EINVAL, "dev_d must be 4-byte aligned");
   if (!std::isfinite(weight)) return fail(PW_EINVAL, "weight must be finite");
   h->kind = SRC_DIAGONAL;
   h->diag = dev_d;
@@ -1086,12 +1094,14 @@ pw_status pw_get_sampling(const pw_csd* h, double* d_m) {
 pw_status pw_spectral_density(pw_csd* h, float* dev_S) {
   g_err.clear();
   if (!h || !dev_S) return fail(PW_EINVAL, "null argument");
+  if (!aligned(dev_S, 4)) return fail(PW_EINVAL, "dev_S must be 4-byte aligned");
   return s_mu(h, 0, 0, dev_S, nullptr);
 }
 
 pw_status pw_degree_of_coherence(pw_csd* h, int iP, int jP, pw_c32* dev_mu) {
   g_err.clear();
   if (!h || !dev_mu) return fail(PW_EINVAL, "null argument");
+  if (!aligned(dev_mu, 8)) return fail(PW_EINVAL, "dev_mu must be 8-byte aligned");
   if (iP < 0 || jP < 0 || iP >= h->N || jP >= h->N)
     return fail(PW_EINVAL, "P1 = (%d, %d) outside the %d x %d grid", iP, jP, h->N, h->N);
   return s_mu(h, iP, jP, nullptr, dev_mu);

@@ -97,6 +97,11 @@ def record(name, **errs):
 # about 1e-7 max|W| everywhere, so mu = W(P1,x)/sqrt(S(P1) S(x)) carries an error of about
 # 1e-7 / sqrt(S(x)/max S): 1e-5 needs S(x)/max S >= ~1e-4.
 MU_REGION = 1e-4
+# In the wider region S(x) >= 1e-6 max S the same model gives ~1e-4 per point at the region's
+# edge; the rel-L2 over the region is dominated by the brighter points.  It is asserted against
+# a stated bound so that a regression there is caught.
+MU_WIDE_REGION = 1e-6
+MU_WIDE_BOUND = 5e-5
 
 
 def check_s_mu(out, Wref, P1, tol=1e-5, name=None):
@@ -105,11 +110,13 @@ def check_s_mu(out, Wref, P1, tol=1e-5, name=None):
     eS = rel(out["S"], Sref)
     sel = Sref >= MU_REGION * Sref.max()
     emu = rel(out["mu"][sel], muref[sel])
-    emu6 = rel(out["mu"][Sref >= 1e-6 * Sref.max()], muref[Sref >= 1e-6 * Sref.max()])
+    wide = Sref >= MU_WIDE_REGION * Sref.max()
+    emu6 = rel(out["mu"][wide], muref[wide])
     eW = rel(out["W"], Wref) if "W" in out else 0.0
     if name:
         record(name, W=eW, S=eS, mu=emu, mu_1e6=emu6)
     assert eS < tol, "S rel-L2 %.3e" % eS
     assert emu < tol, "mu rel-L2 %.3e" % emu
+    assert emu6 < MU_WIDE_BOUND, "mu rel-L2 %.3e in the region S >= 1e-6 max S" % emu6
     assert np.abs(out["mu"]).max() <= 1 + 1e-5
     return eS, emu

@@ -82,6 +82,11 @@ def test_create_rejects_small_and_overlapping_buffers(lib):
         lib.pw_csd_create(32, 20e-6, 633e-9, FAKE_W, nb, FAKE_W + 8, nb)
     with pytest.raises(lib.PwError, match="non-null"):
         lib.pw_csd_create(32, 20e-6, 633e-9, 0, nb, FAKE_WORK, nb)
+    # the CSDA buffers are moved by 16-byte bulk and tensor copies
+    with pytest.raises(lib.PwError, match="16-byte aligned"):
+        lib.pw_csd_create(32, 20e-6, 633e-9, FAKE_W + 8, nb, FAKE_WORK, nb)
+    with pytest.raises(lib.PwError, match="16-byte aligned"):
+        lib.pw_csd_create(32, 20e-6, 633e-9, FAKE_W, nb, FAKE_WORK + 4, nb)
 
 
 def test_null_handle_is_rejected(lib):

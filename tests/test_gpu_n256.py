@@ -1,6 +1,9 @@
-"""N = 256 (four streaming passes; the cluster engine in the tensor-core comparison mode): the phase-screen GSM workload
-(N = 256, dxi = 20 um, lambda = 633 nm, z = 0.5 m, unit-modulus screen with 3 px correlation)
-against the oracle's row probes, plus Hermiticity, power and trace conservation (GPU); and the
+"""N = 256: the phase-screen GSM workload (N = 256, dxi = 20 um, lambda = 633 nm, z = 0.5 m,
+unit-modulus screen with 3 px correlation) against the oracle: 65 output rows spread over the grid
+(edges included) from the row route of Eq. W_fresnel, 16 random bilinear probes u^H W_B v over the
+whole array from W0 through the kernel sums of Eq. W_general, S and mu at the rows' points, plus
+Hermiticity, power and trace conservation (GPU); a non-Hermitian uploaded array on the four
+streaming passes; and the
 same workload with the first radix-16 stage on the tensor cores (split-BF16x3), whose FP64
 errors for W, S and mu are printed next to those of the FP32 path."""
 import numpy as np
@@ -12,9 +15,33 @@ import workloads as WL
 pytestmark = pytest.mark.gpu
 
 
+# 64 output rows spread over the grid, edges included (8 x 8 point-1 positions)
+ROW_IDX = (0, 1, 64, 120, 128, 137, 200, 255)
+ROWS_64 = [(a, b) for a in ROW_IDX for b in (0, 3, 70, 122, 128, 140, 190, 255)]
+
+
+def _probe_fields(N, K, seed):
+    u = WL.uniform01(seed, 4 * K * N * N).reshape(4, K, N, N)
+    return (u[0] - 0.5) + 1j * (u[1] - 0.5), (u[2] - 0.5) + 1j * (u[3] - 0.5)
+
+
+def _gpu_probes(W, U, V):
+    """u_k^H W v_k of the device CSDA (N^2 x N^2 matrix), accumulated in complex128 on the device."""
+    import torch
+    N, K = W.shape[0], U.shape[0]
+    M = W.view(N * N, N * N)
+    Vt = torch.from_numpy(np.ascontiguousarray(V.reshape(K, N * N).T)).cuda()
+    Mv = torch.empty((N * N, K), dtype=torch.complex128, device="cuda")
+    for r0 in range(0, N * N, 2048):
+        Mv[r0:r0 + 2048] = M[r0:r0 + 2048].to(torch.complex128) @ Vt
+    Ut = torch.from_numpy(U.reshape(K, N * N)).cuda()
+    return (torch.conj(Ut) * Mv.T).sum(1).cpu().numpy()
+
+
 def test_phase_screen_n256():
     import torch
     import paper_2203_02734_gb300 as pw
+    from gpu_cases import record
 
     cfg = WL.PHASE_SCREEN_N256
     N, dxi, lam, z = cfg["N"], cfg["dxi"], cfg["lam"], cfg["z"]
@@ -24,12 +51,15 @@ def test_phase_screen_n256():
     c.source_gsm(cfg["sigma_S"], cfg["sigma_mu"], cfg["A"])
     c.source_mask(mt)
     c.propagate_fresnel(z)
+    P1 = tuple(cfg["P1"])
     S = c.spectral_density()
+    mu = c.degree_of_coherence(*P1)
     pw.pw_csd_check(c.h)
     torch.cuda.synchronize()
-    rows = [cfg["P1"], (120, 137), (140, 122)]
-    Wrows = [c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows]
+    rows = [P1] + ROWS_64
+    Wrows = np.stack([c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows])
     S = S.cpu().numpy().astype(np.float64)
+    mu = mu.cpu().numpy().astype(np.complex128)
     dx = c.sampling()
     # Hermiticity on sampled columns
     wref = np.linalg.norm(Wrows[0])
@@ -42,6 +72,9 @@ def test_phase_screen_n256():
     p2 = 0.0
     for k in range(0, flat.numel(), 1 << 27):
         p2 += float(torch.sum(torch.abs(flat[k:k + (1 << 27)]).double() ** 2))
+    # 16 random bilinear probes u^H W_B v over the whole array
+    U, V = _probe_fields(N, 16, 2022)
+    pg = _gpu_probes(c.W, U, V)
     c.close()
     x, _ = O.axis_coords(N, dxi)
     g = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * cfg["sigma_S"] ** 2)
@@ -53,12 +86,38 @@ def test_phase_screen_n256():
     S0 = np.einsum("aa,bb,ab->ab", g, g, w2)
     assert abs(S.sum() * dx ** 2 / (S0.sum() * dxi ** 2) - 1) < 1e-5
     assert S.min() > -1e-6 * S.max()
+    assert np.abs(mu).max() <= 1 + 1e-5
 
+    # the probes from W0 through the kernel sums of Eq. W_general (no FFT)
+    pr = O.bilinear_probes_gsm(m, N, dxi, lam, z, cfg["sigma_S"], cfg["sigma_mu"], cfg["A"], U, V)
+    rms = np.sqrt(np.mean(np.abs(pr) ** 2))
+    ep = np.abs(pg - pr).max() / rms
+    # 64 rows (and P1's row) against the oracle's row probes (Eq. W_fresnel row by row)
     probe = O.propagate_rows_gsm(m, N, dxi, lam, z, cfg["sigma_S"], cfg["sigma_mu"], cfg["A"], rows)
-    for r, (a, b) in enumerate(rows):
-        err = np.linalg.norm(Wrows[r] - probe[r]) / np.linalg.norm(probe[r])
-        assert err < 1e-5, (a, b, err)
-        assert abs(S[a, b] - probe[r][a, b].real) < 1e-5 * np.abs(probe[0]).max()
+    erows = rel(Wrows, probe)
+    rmax = np.linalg.norm(probe, axis=(1, 2)).max()
+    eworst = max(np.linalg.norm(Wrows[r] - probe[r]) for r in range(len(rows))) / rmax
+    # S at the rows' own points and mu(P1, x) at those points (S from each row's diagonal entry)
+    pts = rows[1:]
+    S_ref = np.array([probe[1 + k][a, b].real for k, (a, b) in enumerate(pts)])
+    S_gpu = np.array([S[a, b] for a, b in pts])
+    eS = np.linalg.norm(S_gpu - S_ref) / np.linalg.norm(S_ref)
+    S_P1 = probe[0][P1].real
+    keep = S_ref >= 1e-4 * S_ref.max()
+    mu_ref = np.array([probe[0][a, b] / np.sqrt(S_P1 * S_ref[k]) for k, (a, b) in enumerate(pts)])
+    mu_gpu = np.array([mu[a, b] for a, b in pts])
+    emu = np.linalg.norm((mu_gpu - mu_ref)[keep]) / np.linalg.norm(mu_ref[keep])
+    record("phase_screen_n256", W_rows=erows, W_row_worst=eworst, probes=ep, S_pts=eS, mu_pts=emu,
+           mu_pts_kept=float(keep.sum()))
+    assert ep < 1e-5, ep
+    assert erows < 1e-5, erows
+    assert eworst < 1e-5, eworst
+    assert eS < 1e-5, eS
+    assert emu < 1e-5, emu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
 def test_n256_general_array():

@@ -38,15 +38,22 @@ def _gpu(N, Nz, setup, z, farfield=False, dxi=D, lam=LAM, mode=1):
     return W, S, mu, dx
 
 
-def _check(W, S, mu, dx, Wr, dxr):
+def _check(W, S, mu, dx, Wr, dxr, name=None):
+    """W, S and mu (where S >= 1e-4 max S) within a relative L2 error of 1e-5 of the oracle."""
+    from gpu_cases import record
     N = W.shape[0]
     assert dx == pytest.approx(dxr, rel=1e-12)
-    assert rel(W, Wr) < 1e-5
+    eW = rel(W, Wr)
     Sr = np.real(O.spectral_density(Wr))
-    assert np.abs(S - Sr).max() < 1e-5 * np.abs(Sr).max()
+    eS = rel(S, Sr)
     mur = O.degree_of_coherence(Wr, N // 2, N // 2)
     keep = Sr >= 1e-4 * Sr.max()
-    assert np.abs(mu - mur)[keep].max() < 1e-4
+    emu = rel(mu[keep], mur[keep])
+    if name:
+        record(name, W=eW, S=eS, mu=emu)
+    assert eW < 1e-5, eW
+    assert eS < 1e-5, eS
+    assert emu < 1e-5, emu
 
 
 @MODES
@@ -61,7 +68,7 @@ def test_padded_gsm_aperture_lens(N, Nz, farfield, mode):
     W, S, mu, dx = _gpu(N, Nz, setup, z, farfield, mode=mode)
     m = O.circle_aperture(N, D, radius) * O.thin_lens(N, D, LAM, f)
     Wr, dxr = O.propagate_padded(O.apply_mask(O.gsm_source(N, D, SS, SM), m), D, LAM, z, Nz, farfield)
-    _check(W, S, mu, dx, Wr, dxr)
+    _check(W, S, mu, dx, Wr, dxr, name="padded_n%d_nz%d_%s_mode%d" % (N, Nz, "ff" if farfield else "fr", mode))
 
 
 @MODES
@@ -75,7 +82,7 @@ def test_no_fft_plan_grid_unpadded(mode):
     W, S, mu, dx = _gpu(N, N, setup, 0.5, mode=mode)
     Wr, dxr = O.propagate_fft(O.apply_mask(O.gsm_source(N, D, SS, SM), O.circle_aperture(N, D, 0.3 * N * D)),
                               D, LAM, 0.5)
-    _check(W, S, mu, dx, Wr, dxr)
+    _check(W, S, mu, dx, Wr, dxr, name="dense_n20_mode%d" % mode)
 
 
 @MODES
@@ -107,7 +114,7 @@ def test_padded_diagonal_source(mode):
     i = np.arange(N)
     W0[i[:, None], i[None, :], i[:, None], i[None, :]] = d
     Wr, dxr = O.propagate_padded(W0, D, LAM, 2.0, Nz, farfield=True)
-    _check(W, S, mu, dx, Wr, dxr)
+    _check(W, S, mu, dx, Wr, dxr, name="padded_diag_mode%d" % mode)
 
 
 def test_padded_two_plane_chain():
@@ -275,16 +282,19 @@ def test_tensor_core_single_a_tile_n240():
         assert rel(Wrows[r], ref[r]) < 1e-5
 
 
-def test_tensor_core_wait_timeout_is_reported_and_recovers():
-    # failure detection without a GPU fault: CTA 0 never copies operand chunk 1, its bounded wait
-    # gives up (~1 s), pw_csd_check reports PW_ETIMEOUT, and the next propagation is right
+@pytest.mark.parametrize("stall", [1, -2], ids=["b_copy_left_out", "a_tile_left_out"])
+def test_tensor_core_wait_timeout_is_reported_and_recovers(stall):
+    # failure detection without a GPU fault: CTA 0 never copies operand chunk 1 (stall = 1), or never
+    # announces A tile 2 while that chunk's B copy is in flight (stall = -2); the bounded wait gives
+    # up (~1 s), the kernel drains what it started, pw_csd_check reports PW_ETIMEOUT, and the next
+    # propagation is right
     import paper_2203_02734_gb300 as pw
     N, Nz, z = 40, 64, 0.4  # Np = 48: three operand chunks
     c = pw.CSD(N, D, LAM)
     pw.pw_csd_set_padding(c.h, Nz)
     pw.pw_csd_set_dft_mode(c.h, pw.PW_DFT_TC_BF16X3)
     c.source_gsm(SS, SM, 1.0)
-    pw.pw_csd_inject_stall(c.h, 1)
+    pw.pw_csd_inject_stall(c.h, stall)
     c.propagate_fresnel(z)
     with pytest.raises(pw.PwError, match="PW_ETIMEOUT"):
         pw.pw_csd_check(c.h)

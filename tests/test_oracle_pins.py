@@ -415,3 +415,43 @@ def test_padded_rows_match_padded_route_far_field():
     r = O.propagate_rows_gsm_padded(m, N, DXI, LAM, 2.0, 0.1e-3, 0.05e-3, 1.0, rows, Nz, farfield=True)
     for k, (i, j) in enumerate(rows):
         assert np.linalg.norm(r[k] - a[i, j]) / np.linalg.norm(a[i, j]) < 1e-12
+
+
+# --------------------------------------------------------------------------- bilinear probes
+def _probe_fields(N, K, seed):
+    u = WL.uniform01(seed, 4 * K * N * N).reshape(4, K, N, N)
+    return (u[0] - 0.5) + 1j * (u[1] - 0.5), (u[2] - 0.5) + 1j * (u[3] - 0.5)
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_bilinear_probes_match_fft_route(farfield):
+    """u^H W_B v from W0 through the kernel sums (no FFT) == the same form of Algorithm 2's output,
+    and of the brute-force quadrature; a random non-Hermitian W0 at N = 6, 8."""
+    for N in (6, 8):
+        rng = np.random.default_rng(N)
+        W0 = rng.standard_normal((N,) * 4) + 1j * rng.standard_normal((N,) * 4)
+        U, V = _probe_fields(N, 3, 40 + N)
+        got = O.bilinear_probes(W0, DXI, LAM, 0.45, U, V, farfield)
+        WB, _ = O.propagate_fft(W0, DXI, LAM, 0.45, farfield)
+        Wd, _ = O.propagate_direct(W0, DXI, LAM, 0.45, farfield)
+        M, Md = WB.reshape(N * N, N * N), Wd.reshape(N * N, N * N)
+        want = np.array([np.conj(U[k].ravel()) @ M @ V[k].ravel() for k in range(3)])
+        want_d = np.array([np.conj(U[k].ravel()) @ Md @ V[k].ravel() for k in range(3)])
+        assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()
+        assert np.abs(got - want_d).max() < 1e-11 * np.abs(want).max()
+        # a probe is not symmetric in u and v: swapping them changes the value
+        swapped = O.bilinear_probes(W0, DXI, LAM, 0.45, V, U, farfield)
+        assert np.abs(swapped - got).max() > 1e-3 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_bilinear_probes_gsm_match_general_form(farfield):
+    """The separable masked-GSM form equals bilinear_probes on the materialised source (N = 12,
+    random complex mask: a transposed g or a dropped conjugate of the mask fails this)."""
+    N = 12
+    m = _rand_mask(N, 11)
+    W0 = O.apply_mask(O.gsm_source(N, DXI, SS, SM, 1.7), m)
+    U, V = _probe_fields(N, 4, 90)
+    a = O.bilinear_probes_gsm(m, N, DXI, LAM, 0.6, SS, SM, 1.7, U, V, farfield)
+    b = O.bilinear_probes(W0, DXI, LAM, 0.6, U, V, farfield)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()

@@ -75,3 +75,23 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         pw.pw_propagate_gsm_fresnel_noalloc(64, DXI, LAM, 0.5, SS, SM, 1.0, 0.0, 0.0, 0, W_out.data_ptr(),
                                             64 ** 4 * 8, W_out.data_ptr(), 0)
     assert "PW_EINVAL" in str(e.value) and "maximum N = 32" in str(e.value)
+
+
+def test_noalloc_rejects_misaligned_pointers():
+    # W is written by bulk copies (16-byte aligned addresses), S as floats, the mask as 8-byte
+    # complex values: misaligned pointers return PW_EINVAL on the host, before any launch.
+    import torch
+    import paper_2203_02734_gb300 as pw
+
+    N = 8
+    W_out = torch.empty(N ** 4 + 2, dtype=torch.complex64, device="cuda")
+    S_out = torch.empty(N * N + 1, dtype=torch.float32, device="cuda")
+    mask = torch.ones(N * N + 1, dtype=torch.complex64, device="cuda")
+    nb = N ** 4 * 8
+    bad = [(W_out.data_ptr() + 8, S_out.data_ptr(), 0, "dev_W_out must be 16-byte aligned"),
+           (W_out.data_ptr(), S_out.data_ptr() + 2, 0, "dev_S_out must be 4-byte aligned"),
+           (W_out.data_ptr(), S_out.data_ptr(), mask.data_ptr() + 4, "dev_mask must be 8-byte aligned")]
+    for w, s, m, msg in bad:
+        with pytest.raises(pw.PwError) as e:
+            pw.pw_propagate_gsm_fresnel_noalloc(N, DXI, LAM, 0.5, SS, SM, 1.0, 0.0, 0.0, m, w, nb, s, 0)
+        assert "PW_EINVAL" in str(e.value) and msg in str(e.value)
