@@ -34,6 +34,7 @@ __all__ = [
     "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
     "propagate_rows_gsm", "s_loss", "s_loss_gradient", "propagate_padded", "padded_dft_matrix",
     "propagate_rows_gsm_padded", "axis_kernels", "bilinear_probes", "bilinear_probes_gsm",
+    "sm_loss", "adjoint_source", "sm_loss_gradient",
 ]
 
 
@@ -533,3 +534,77 @@ def s_loss_gradient(sigma_S, sigma_mu, A, amask, N, dxi, lam, z, S_target, weigh
     AG = A * G
     ga = 2.0 * np.real(np.einsum("abcd,abcd,cd->ab", cW, AG, amask) + np.einsum("abcd,abcd,ab->cd", cW, AG, amask))
     return L, gS, gM, gA, ga
+
+
+def sm_loss(W0, dxi, lam, z, P1, S_target, wS, mu_target, wmu, farfield=False):
+    """Least-squares loss on S and mu of the propagated CSDA (Algorithm 4, Algorithm coherence):
+      L = sum_x wS(x) (S_B(x) - S_target(x))^2 + sum_x wmu(x) |mu_B(P1, x) - mu_target(x)|^2.
+    Returns (L, W_B, S_B, mu_B)."""
+    WB, _ = propagate_fft(W0, dxi, lam, z, farfield)
+    S = np.real(spectral_density(WB))
+    mu = degree_of_coherence(WB, *P1)
+    L = float(np.sum(wS * (S - S_target) ** 2) + np.sum(wmu * np.abs(mu - mu_target) ** 2))
+    return L, WB, S, mu
+
+
+def adjoint_source(WB, P1, gS, gmu):
+    """dL/dW_B* of a loss L(S_B, mu_B) given the real gradients gS = dL/dS_B (N x N) and
+    gmu = dL/dRe mu + i dL/dIm mu (N x N) of mu_B(P1, .) (reading R22).  With S(x) = Re W_B(x, x),
+    w(x) = W_B(P1, x), D(x) = sqrt(S(P1) S(x)) and mu = w / D (0 where D = 0, held constant there):
+      dmu = dw / D - (mu / 2) (dS(P1) / S(P1) + dS(x) / S(x)),
+    so with r(x) = Re(conj(gmu(x)) mu(x)) the loss sees
+      dL/dS(y) = gS(y) - r(y) / (2 S(y)) - [y = P1] sum_x r(x) / (2 S(P1)),
+      dL/dw(x) (real gradient) = gmu(x) / D(x),
+    and dL/dW_B* is half the real gradient: (1/2) dL/dS(y) on the diagonal (y, y) plus
+    (1/2) gmu(x) / D(x) on the row (P1, x).  Returns that N^4 array (not Hermitian)."""
+    N = WB.shape[0]
+    S = np.real(spectral_density(WB))
+    iP, jP = P1
+    D = np.sqrt(np.maximum(S * S[iP, jP], 0.0))
+    ok = D > 0
+    mu = np.zeros((N, N), dtype=np.complex128)
+    mu[ok] = WB[iP, jP][ok] / D[ok]
+    gmu = np.where(ok, gmu, 0.0)
+    r = np.real(np.conj(gmu) * mu)
+    dS = np.array(gS, dtype=np.float64)
+    okS = ok & (S > 0)
+    dS[okS] -= r[okS] / (2.0 * S[okS])
+    if S[iP, jP] > 0:
+        dS[iP, jP] -= np.sum(r) / (2.0 * S[iP, jP])
+    Y = np.zeros((N, N, N, N), dtype=np.complex128)
+    i = np.arange(N)
+    Y[i[:, None], i[None, :], i[:, None], i[None, :]] = 0.5 * dS
+    gw = np.zeros((N, N), dtype=np.complex128)
+    gw[ok] = gmu[ok] / D[ok]
+    Y[iP, jP] += 0.5 * gw
+    return Y
+
+
+def sm_loss_gradient(sigma_S, sigma_mu, A, amask, N, dxi, lam, z, P1, S_target, wS, mu_target, wmu,
+                     farfield=False):
+    """Gradient of sm_loss for the amplitude-masked GSM source W0 = A a(xi1) a(xi2) G by the adjoint
+    (readings R16-R18, R22): Y = adjoint_source, W0bar = P^H(Y) (propagate_adjoint), and for each
+    real parameter theta, dL/dtheta = 2 Re sum conj(W0bar) dW0/dtheta with the derivatives listed
+    in s_loss_gradient.  Also returns the real gradient with respect to W0 itself (a general complex
+    N^4 array), 2 W0bar.  Returns (L, dL/dsigma_S, dL/dsigma_mu, dL/dA, dL/da, dL/dW0)."""
+    amask = np.asarray(amask, dtype=np.float64)
+    W0 = apply_mask(gsm_source(N, dxi, sigma_S, sigma_mu, A), amask)
+    L, WB, S, mu = sm_loss(W0, dxi, lam, z, P1, S_target, wS, mu_target, wmu, farfield)
+    gS = 2.0 * wS * (S - S_target)
+    gmu = 2.0 * wmu * (mu - mu_target)
+    Y = adjoint_source(WB, P1, gS, gmu)
+    W0bar = propagate_adjoint(Y, dxi, lam, z, farfield)
+    G = gsm_source(N, dxi, sigma_S, sigma_mu, 1.0).real
+    x, y = axis_coords(N, dxi)
+    r2 = x[:, None] ** 2 + y[None, :] ** 2
+    R1 = r2[:, :, None, None]
+    R2 = r2[None, None, :, :]
+    D2 = (x[:, None, None, None] - x[None, None, :, None]) ** 2 + (y[None, :, None, None] - y[None, None, None, :]) ** 2
+    cW = np.conj(W0bar)
+    W0r = np.real(W0)
+    gA = 2.0 * np.real(np.sum(cW * W0r / A))
+    gS_ = 2.0 * np.real(np.sum(cW * W0r * (R1 + R2) / (2.0 * sigma_S ** 3)))
+    gM = 2.0 * np.real(np.sum(cW * W0r * D2 / sigma_mu ** 3))
+    AG = A * G
+    ga = 2.0 * np.real(np.einsum("abcd,abcd,cd->ab", cW, AG, amask) + np.einsum("abcd,abcd,ab->cd", cW, AG, amask))
+    return L, gS_, gM, gA, ga, 2.0 * W0bar

@@ -455,3 +455,81 @@ def test_bilinear_probes_gsm_match_general_form(farfield):
     a = O.bilinear_probes_gsm(m, N, DXI, LAM, 0.6, SS, SM, 1.7, U, V, farfield)
     b = O.bilinear_probes(W0, DXI, LAM, 0.6, U, V, farfield)
     assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+# --------------------------------------------------------------------------- mu-loss adjoint
+def _sm_problem(N, farfield):
+    P1 = (N // 2 - 1, N // 2 + 1)
+    amask = 0.5 + 0.5 * WL.uniform01(77, N * N).reshape(N, N)
+    S_t = 0.7 * np.ones((N, N)) * 1e-3
+    mu_t = 0.3 * np.exp(1j * np.linspace(0, 1, N * N)).reshape(N, N)
+    wS = 1e6 * (0.5 + WL.uniform01(78, N * N).reshape(N, N))
+    wmu = 0.5 + WL.uniform01(79, N * N).reshape(N, N)
+    return P1, amask, S_t, wS, mu_t, wmu
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_sm_loss_gradient_matches_central_differences(farfield):
+    """Adjoint gradient of a loss on S and mu (reading R22) against central finite differences of
+    the forward loss in FP64: sigma_S, sigma_mu, A and two mask pixels (N = 8, z = 0.35 m)."""
+    N, z = 8, 0.35
+    P1, amask, S_t, wS, mu_t, wmu = _sm_problem(N, farfield)
+    sS, sM, A = 0.09e-3, 0.06e-3, 1.3
+
+    def L(sS_, sM_, A_, am_):
+        W0 = O.apply_mask(O.gsm_source(N, DXI, sS_, sM_, A_), am_)
+        return O.sm_loss(W0, DXI, LAM, z, P1, S_t, wS, mu_t, wmu, farfield)[0]
+    L0, gS, gM, gA, ga, _ = O.sm_loss_gradient(sS, sM, A, amask, N, DXI, LAM, z, P1, S_t, wS, mu_t, wmu, farfield)
+    assert L0 > 0
+
+    def cd(f, x, h):
+        return (f(x + h) - f(x - h)) / (2 * h)
+    fS = cd(lambda v: L(v, sM, A, amask), sS, 1e-6 * sS)
+    fM = cd(lambda v: L(sS, v, A, amask), sM, 1e-6 * sM)
+    fA = cd(lambda v: L(sS, sM, v, amask), A, 1e-6 * A)
+    for g, f in [(gS, fS), (gM, fM), (gA, fA)]:
+        assert abs(g - f) <= 1e-6 * abs(f), (g, f)
+    for (i, j) in [(3, 4), (P1[0], P1[1])]:
+        def Lm(v, i=i, j=j):
+            am = amask.copy()
+            am[i, j] = v
+            return L(sS, sM, A, am)
+        f = cd(Lm, amask[i, j], 1e-6)
+        assert abs(ga[i, j] - f) <= 1e-6 * max(abs(f), 1e-3 * np.abs(ga).max()), (i, j, ga[i, j], f)
+
+
+def test_sm_loss_gradient_in_w0_matches_central_differences():
+    """The real gradient with respect to a general complex W0 (not only Hermitian perturbations):
+    central differences of the loss in Re and Im of single entries, one of them on the P1 row."""
+    N, z = 6, 0.4
+    P1, _, S_t, wS, mu_t, wmu = _sm_problem(N, False)
+    # a GSM source plus a random Hermitian part: S stays well away from zero, so mu is smooth enough
+    # for central differences with a step of 1e-6 max |W0|
+    R = WL.random_csd(N, seed=12, n_modes=3)
+    W0 = O.gsm_source(N, DXI, SS, SM) + 0.1 * R / np.abs(R).max()
+    L0, WB, S, mu = O.sm_loss(W0, DXI, LAM, z, P1, S_t, wS, mu_t, wmu)
+    Y = O.adjoint_source(WB, P1, 2.0 * wS * (S - S_t), 2.0 * wmu * (mu - mu_t))
+    g = 2.0 * O.propagate_adjoint(Y, DXI, LAM, z)
+    h = 1e-6 * np.abs(W0).max()
+    for idx in [(1, 2, 3, 4), (P1[0], P1[1], 0, 5), (2, 2, 2, 2)]:
+        for unit in (1.0, 1j):
+            Wp, Wm = W0.copy(), W0.copy()
+            Wp[idx] += unit * h
+            Wm[idx] -= unit * h
+            f = (O.sm_loss(Wp, DXI, LAM, z, P1, S_t, wS, mu_t, wmu)[0]
+                 - O.sm_loss(Wm, DXI, LAM, z, P1, S_t, wS, mu_t, wmu)[0]) / (2 * h)
+            got = g[idx].real if unit == 1.0 else g[idx].imag
+            assert abs(got - f) <= 1e-6 * np.abs(g).max(), (idx, unit, got, f)
+
+
+def test_adjoint_source_reduces_to_s_loss():
+    """With no mu term the adjoint source is the diagonal (1/2) dL/dS of s_loss_gradient (R18)."""
+    N = 6
+    W0 = O.gsm_source(N, DXI, SS, SM)
+    WB, _ = O.propagate_fft(W0, DXI, LAM, 0.5)
+    gS = WL.uniform01(5, N * N).reshape(N, N)
+    Y = O.adjoint_source(WB, (2, 3), gS, np.zeros((N, N)))
+    i = np.arange(N)
+    D = np.zeros_like(Y)
+    D[i[:, None], i[None, :], i[:, None], i[None, :]] = 0.5 * gS
+    assert np.abs(Y - D).max() == 0
