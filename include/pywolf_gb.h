@@ -155,6 +155,43 @@ pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double
                           const float* dev_amask, double lambda_m, double z_m, int farfield,
                           double* dev_grad3, float* dev_grad_mask);
 
+/* The adjoint of one propagation for a real loss L on S and mu of its output plane (the paper has
+ * no adjoint; it is the transpose of the linear map of Eq. W_fresnel / Eq. W_farfield, reading R17).
+ * Upstream gradients follow the real convention g = dL/dRe + i dL/dIm (torch's for complex
+ * tensors).  With S(x) = Re W_B(x, x) (Algorithm 4) and mu(x) = W_B(P1, x) / sqrt(S(P1) S(x))
+ * (Algorithm coherence, 0 where S(P1) S(x) <= 0), dL/dW_B* is (1/2) dL/dS on the diagonal plus
+ * (1/2) gmu / sqrt(S(P1) S(x)) on the row of P1, dL/dS taking the mu term through S (reading R22);
+ * the call builds that source in-kernel, propagates it back (P^H, Fresnel over z from the output
+ * sampling dx onto the source grid d = lambda z / (N dx)) and forms the requested gradients:
+ *   dev_grad3 / dev_grad_amask: dL/d(sigma_S, sigma_mu, A) and dL/da of the amplitude-masked GSM
+ *     source W0 = A a(xi1) a(xi2) G (Sec. 5.4) that the forward propagation started from, reduced
+ *     in the epilogue of the adjoint's second pass (W0bar is never stored; at N = 256 it goes
+ *     through dev_W and one gradient kernel);
+ *   grad_W0: dL/dRe W0 + i dL/dIm W0 for W0 taken as a general complex N^4 array, written into
+ *     dev_W (a second, non-Hermitian adjoint propagation when both kinds are asked with a mu term).
+ * The handle's current sampling must be the forward's output sampling dx (true right after the
+ * forward propagation, or after pw_csd_reset(h, dx)); the current plane's contents are not used.
+ * dev_work is used as scratch; dev_W is overwritten (the gradient with grad_W0, else unspecified).
+ * On return the handle is at the source plane (sampling d) with no source recorded.  Asynchronous
+ * on the handle's stream.
+ * Errors: PW_EINVAL for a null or misaligned pointer, a P1 outside the grid, dev_dmu without
+ * dev_S / dev_mu, no upstream gradient or no output, invalid GSM parameters with dev_grad3 /
+ * dev_grad_amask; PW_EUNSUPPORTED on a zero-padded grid or one without an FFT plan. */
+typedef struct pw_adjoint {
+  const float* dev_dS;     /* N x N dL/dS of the output plane (float32, device), or NULL */
+  const pw_c32* dev_dmu;   /* N x N dL/dRe mu + i dL/dIm mu of mu(P1, .) (device), or NULL */
+  int iP, jP;              /* P1 of mu */
+  const float* dev_S;      /* N x N S of the output plane (device), needed with dev_dmu */
+  const pw_c32* dev_mu;    /* N x N mu(P1, .) of the output plane (device), needed with dev_dmu */
+  double sigma_S_m, sigma_mu_m, amplitude;  /* the forward's GSM source, for dev_grad3 / dev_grad_amask */
+  const float* dev_amask;  /* N x N real amplitude mask a of that source (device), or NULL for a = 1 */
+  double* dev_grad3;       /* out: [dL/dsigma_S, dL/dsigma_mu, dL/dA] (3 doubles, device), or NULL */
+  float* dev_grad_amask;   /* out: N x N dL/da (float32, device), or NULL */
+  int grad_W0;             /* nonzero: write dL/dRe W0 + i dL/dIm W0 (N^4 complex64) into dev_W */
+} pw_adjoint;
+pw_status pw_propagate_fresnel_adjoint(pw_csd* h, double z_m, const pw_adjoint* a);
+pw_status pw_propagate_farfield_adjoint(pw_csd* h, double z_m, const pw_adjoint* a);
+
 /* Fresnel propagation over distance z_m > 0 (Eq. W_fresnel; Algorithm 2 without the
  * far-field switch).  Result: dev_W holds W at the new plane, sampling lambda z/(N d);
  * S of the new plane is computed on the way.  Returns PW_ESTATE if no source was set. */

@@ -293,8 +293,8 @@ def _probe_vectors(U, V, N, dxi, lam, z, farfield):
     Hx, Hy = axis_kernels(N, dxi, lam, z, farfield)
     U = np.asarray(U, dtype=np.complex128).reshape(-1, N, N)
     V = np.asarray(V, dtype=np.complex128).reshape(-1, N, N)
-    al = np.einsum("ai,kab,bj->kij", Hx, U, Hy)
-    be = np.einsum("ai,kab,bj->kij", Hx, V, Hy)
+    al = np.matmul(np.matmul(Hx.T, U), Hy)
+    be = np.matmul(np.matmul(Hx.T, V), Hy)
     return al, be
 
 

@@ -89,6 +89,24 @@ for _name, (_res, _args) in {
     _f.argtypes = _args
 
 
+class pw_adjoint(ctypes.Structure):
+    """Mirror of the C struct pw_adjoint (include/pywolf_gb.h)."""
+    _fields_ = [("dev_dS", _vp), ("dev_dmu", _vp), ("iP", _i), ("jP", _i), ("dev_S", _vp), ("dev_mu", _vp),
+                ("sigma_S_m", _d), ("sigma_mu_m", _d), ("amplitude", _d), ("dev_amask", _vp),
+                ("dev_grad3", _vp), ("dev_grad_amask", _vp), ("grad_W0", _i)]
+
+
+_AP = ctypes.POINTER(pw_adjoint)
+for _name, (_res, _args) in {
+    "pw_propagate_fresnel_adjoint": (_i, [_vp, _d, _AP]),
+    "pw_propagate_farfield_adjoint": (_i, [_vp, _d, _AP]),
+}.items():
+    SIGNATURES[_name] = (_res, _args)
+    _f = getattr(LIB, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
 class PwError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (LIB.pw_status_string(status).decode(), msg))
@@ -299,3 +317,12 @@ def pw_batch_inject_stall(b, instance, wait_s):
 
 def pw_batch_destroy(b):
     _check(LIB.pw_batch_destroy(b))
+
+
+def pw_propagate_fresnel_adjoint(h, z_m, adj):
+    """adj: a pw_adjoint (device addresses as integers, 0 for NULL)."""
+    _check(LIB.pw_propagate_fresnel_adjoint(h, z_m, ctypes.byref(adj)))
+
+
+def pw_propagate_farfield_adjoint(h, z_m, adj):
+    _check(LIB.pw_propagate_farfield_adjoint(h, z_m, ctypes.byref(adj)))

@@ -176,9 +176,11 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
-    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM || SRC == SRC_ADJ) s_ab = cscale(s_ab, p.A);
     if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    AdjSlice adj{};
+    if (SRC == SRC_ADJ) adj = adj_slice(p, ab, N);
     float2 v[2][16];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(Geo<CS>::NT, Geo<CS>::MINB)
         float2 x = cmul(sc, SRC == SRC_GSM ? cscale(ein[d], gB[d]) : ein[d]);
         if (MASK) x = cmul(x, __ldg(mask + c * N + d));
         if (ARRAY) x = cmul(x, __ldg(W0 + (size_t)c * N + d));
+        if (SRC == SRC_ADJ) x = cmul(x, adj.at(p.cross, c * N + d));
         bool keep = inside(c, d);
         if (DIAG) keep = keep && c == a && d == b;
         v[h][r] = keep ? x : make_float2(0.f, 0.f);

@@ -38,8 +38,9 @@ __global__ void gsm_gradient_tables(GradArgs g) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
     const int i = idx / N, k = idx - i * N;
     const double xi = (i - M) * d, xk = (k - M) * d;
-    g.gtab[idx] = (float)exp(-(xi * xi + xk * xk) / (4 * g.sigma_S * g.sigma_S) -
-                             (xi - xk) * (xi - xk) / (2 * g.sigma_mu * g.sigma_mu));
+    if (g.sigma_S > 0.0)
+      g.gtab[idx] = (float)exp(-(xi * xi + xk * xk) / (4 * g.sigma_S * g.sigma_S) -
+                               (xi - xk) * (xi - xk) / (2 * g.sigma_mu * g.sigma_mu));
     if (idx < N) {
       const double n2 = (double)(idx - M) * (idx - M);
       g.qtab[idx] = cis_turns(frac_turns(n2 * g.Kq));
@@ -148,6 +149,81 @@ __global__ void __launch_bounds__(256) gsm_gradient_reduce(GradArgs g) {
     const double s3 = g.sigma_S * g.sigma_S * g.sigma_S, m3 = g.sigma_mu * g.sigma_mu * g.sigma_mu;
     const double scale = threadIdx.x == 0 ? g.A / s3 : (threadIdx.x == 1 ? 2.0 * g.A / m3 : 2.0);
     g.g3[threadIdx.x] = g.c * scale * x;
+  }
+}
+
+// ---- the adjoint source of a loss on S and mu (reading R22), on the output plane -----------------
+// Given the real gradients gS = dL/dS and gmu = dL/dRe mu + i dL/dIm mu of mu(P1, .), and S, mu of
+// the output plane: with D(x) = sqrt(S(P1) S(x)), r(x) = Re(conj(gmu(x)) mu(x)) (0 where D = 0),
+//   dL/dS(y) = gS(y) - r(y) / (2 S(y)) - [y = P1] sum_x r(x) / (2 S(P1)),
+//   dL/dW_B* = (1/2) dL/dS(y) on the diagonal (y, y) and (1/2) gmu(x) / D(x) on the row (P1, x).
+// The kernel writes the source of the adjoint propagation, the conjugate of that array: d(y) =
+// (1/2) dL/dS(y) and cross(x) = conj((1/2) gmu(x) / D(x)).  One CTA (the sum over x is a block
+// reduction in FP64, a fixed order).
+struct AdjPrepArgs {
+  int N, iP, jP;
+  const float* gS;     // N x N or nullptr
+  const float2* gmu;   // N x N or nullptr
+  const float* S;      // N x N (with gmu)
+  const float2* mu;    // N x N (with gmu)
+  float* d;            // out: N x N
+  float2* cross;       // out: N x N
+};
+
+__global__ void __launch_bounds__(1024) adjoint_prep_kernel(AdjPrepArgs a) {
+  __shared__ double red[32];
+  const int NN = a.N * a.N, xp = a.iP * a.N + a.jP;
+  const float sp = a.gmu ? a.S[xp] : 0.f;
+  double rs = 0.0;
+  if (a.gmu) {
+    for (int x = threadIdx.x; x < NN; x += blockDim.x) {
+      const float sx = a.S[x];
+      if (sp * sx > 0.f) {
+        const float2 g = a.gmu[x], m = a.mu[x];
+        rs += (double)(g.x * m.x + g.y * m.y);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      red[0] = t;
+    }
+    __syncthreads();
+    rs = red[0];
+  }
+  for (int x = threadIdx.x; x < NN; x += blockDim.x) {
+    float dS = a.gS ? a.gS[x] : 0.f;
+    float2 c = make_float2(0.f, 0.f);
+    if (a.gmu) {
+      const float sx = a.S[x];
+      if (sp * sx > 0.f) {
+        const float2 g = a.gmu[x], m = a.mu[x];
+        if (sx > 0.f) dS -= (g.x * m.x + g.y * m.y) / (2.f * sx);
+        const float inv = rsqrtf(sp * sx);
+        c = make_float2(0.5f * g.x * inv, -0.5f * g.y * inv);
+      }
+      if (x == xp && sp > 0.f) dS -= (float)(rs / (2.0 * (double)sp));
+    }
+    a.d[x] = 0.5f * dS;
+    a.cross[x] = c;
+  }
+}
+
+// dL/dRe W0 + i dL/dIm W0 = 2 W0bar = 2 c conj(R ff) in place over the N^4 array R that the
+// adjoint propagation left in W (ff = q(x1) q*(x2) after a far-field forward propagation).
+__global__ void w0_gradient_kernel(float2* R, int N, float twoc, const float2* __restrict__ qff) {
+  const size_t NN = (size_t)N * N, total = NN * NN;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    float2 r = R[i];
+    if (qff) {
+      const size_t x1 = i / NN, x2 = i - x1 * NN;
+      const int a = (int)(x1 / N), b = (int)(x1 % N), c = (int)(x2 / N), d = (int)(x2 % N);
+      r = cmul(r, cmul(cmul(qff[a], qff[b]), cconj(cmul(qff[c], qff[d]))));
+    }
+    R[i] = make_float2(twoc * r.x, -twoc * r.y);
   }
 }
 

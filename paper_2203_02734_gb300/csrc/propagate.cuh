@@ -85,18 +85,51 @@ static __global__ void tables_kernel(TableArgs t) {
   }
 }
 
-// Source of pass A: the GSM model, an uploaded CSDA, or a diagonal (delta-correlated,
-// incoherent) source W0 = w d(xi1) delta(xi1 - xi2), d real.
-enum SrcMode { SRC_GSM = 0, SRC_ARRAY = 1, SRC_DIAG = 2 };
+// Source of pass A: the GSM model, an uploaded CSDA, a diagonal (delta-correlated, incoherent)
+// source W0 = w d(xi1) delta(xi1 - xi2) with d real, or the adjoint source of a loss on S and mu
+// (SRC_ADJ): the diagonal d plus the row of the coherence point P1,
+//   Y(x1, x2) = d(x1) delta(x1 - x2) + delta(x1 - P1) r(x2),
+// completed to its Hermitian part (r halved on the row, conj(r)/2 on the column of P1) when the
+// propagated array must be Hermitian.
+enum SrcMode { SRC_GSM = 0, SRC_ARRAY = 1, SRC_DIAG = 2, SRC_ADJ = 3 };
 
 struct PassAArgs {
   const float2* F;
   const float* G;
   const float2* tw;
   const float2* W0;   // uploaded source (SRC_ARRAY) or nullptr
-  const float* diag;  // N x N diagonal (SRC_DIAG) or nullptr
-  float A;            // GSM amplitude, or the weight w of the diagonal source
+  const float* diag;  // N x N diagonal (SRC_DIAG, SRC_ADJ) or nullptr
+  float A;            // GSM amplitude, or the weight w of the diagonal / adjoint source
+  const float2* cross;  // SRC_ADJ: N x N row r of P1, or nullptr
+  int iP, jP;           // SRC_ADJ: P1
+  int herm;             // SRC_ADJ: nonzero = Hermitian part (row and column of P1, halved)
 };
+
+// The adjoint source of one slice x1 = ab, evaluated at x2 = cd (SRC_ADJ).
+struct AdjSlice {
+  int ab, p1;
+  float dg;      // d(x1), or 0
+  float2 col;    // conj(r(x1)) / 2 (Hermitian part), or 0
+  bool row;      // x1 == P1: the slice holds the row r
+  float wr;      // weight of the row: 1/2 (Hermitian part) or 1
+  __device__ __forceinline__ float2 at(const float2* __restrict__ cross, int cd) const {
+    float2 v = make_float2(cd == ab ? dg : 0.f, 0.f);
+    if (cd == p1) v = cadd(v, col);
+    if (row) v = cadd(v, cscale(__ldg(cross + cd), wr));
+    return v;
+  }
+};
+
+__device__ __forceinline__ AdjSlice adj_slice(const PassAArgs& p, int ab, int N) {
+  AdjSlice s;
+  s.ab = ab;
+  s.p1 = p.iP * N + p.jP;
+  s.dg = p.diag ? __ldg(p.diag + ab) : 0.f;
+  s.row = p.cross != nullptr && ab == s.p1;
+  s.wr = p.herm ? 0.5f : 1.f;
+  s.col = (p.cross != nullptr && p.herm) ? cscale(cconj(__ldg(p.cross + ab)), 0.5f) : make_float2(0.f, 0.f);
+  return s;
+}
 
 template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
 // Width g of the d' runs of the V layout: 4 (one 32-byte sector per run; 2 when 4 does not
@@ -118,7 +151,7 @@ template <int N> __host__ __device__ constexpr size_t pass_a_smem() {
   return (size_t)N * pitch<N>() * sizeof(float2) + N * sizeof(float2) + 2 * N * sizeof(float);
 }
 template <int N> __host__ __device__ constexpr size_t pass_b_smem() {
-  return (size_t)N * pitch<N>() * sizeof(float2) + 2 * N * sizeof(float2);
+  return (size_t)N * pitch<N>() * sizeof(float2) + 2 * N * sizeof(float2) + 4 * 32 * sizeof(double);
 }
 
 // ---- bulk asynchronous copies (TMA) issued by one thread, tracked as bulk groups ----
@@ -204,13 +237,16 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_con
     }
     __syncthreads();
     float2 s_ab = cconj(__ldg(F + ab));
-    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM || SRC == SRC_ADJ) s_ab = cscale(s_ab, p.A);
     if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    AdjSlice adj{};
+    if (SRC == SRC_ADJ) adj = adj_slice(p, ab, N);
     auto gen = [&](int d, int c) -> float2 {
       const float2 f = __ldg(F + c * N + d);
       if (ARRAY) return cmul(cmul(s_ab, __ldg(W0 + c * N + d)), f);
       if (DIAG) return (c * N + d == ab) ? cmul(s_ab, f) : make_float2(0.f, 0.f);
+      if (SRC == SRC_ADJ) return cmul(cmul(s_ab, f), adj.at(p.cross, c * N + d));
       return cscale(cmul(s_ab, f), gA[c] * gB[d]);
     };
     auto st1 = [buf](int d, int c, float2 v) { buf[c * P + d] = v; };
@@ -231,6 +267,23 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_a_kernel(const __grid_con
   if (threadIdx.x == 0) bulk_wait_all();
 }
 
+// Parameter gradients of the amplitude-masked GSM source W0 = A a(x1) a(x2) G(x1, x2) reduced in
+// the epilogue of the adjoint propagation's second pass (W_GRAD): the array R it computes gives
+// conj(W0bar) = c R ff (ff = q(x1) q*(x2) after a far-field forward propagation, else 1), and per
+// output column x2 the kernel adds, over x1, t = Re(R ff) G(x1, x2) a(x1):
+//   part[x2][0] = a(x2) d^2 sum t (r^2(x1) + r^2(x2)),  part[x2][1] = a(x2) d^2 sum t |x1 - x2|^2,
+//   part[x2][2] = a(x2) sum t  (r^2 and |x1 - x2|^2 in pixels^2),  gmask[x2] = gscale sum t,
+// the same per-point sums the standalone gradient kernel forms row by row (R and G symmetric).
+struct GradEpi {
+  const float* gtab;   // N x N GSM axis factor G(i, k), the same table for both axes
+  const float* amask;  // N x N amplitude mask, or nullptr (a = 1)
+  const float2* qff;   // far field: q(x_i) per axis (N entries), or nullptr
+  double* part;        // N^2 x 3 per-column sums
+  float* gmask;        // N^2 mask gradient (4 c A sum t), or nullptr
+  float gscale;        // 4 c A
+  float d2;            // d^2 of the source grid
+};
+
 struct PassBArgs {
   const float2* V;
   const float2* tw;
@@ -240,11 +293,52 @@ struct PassBArgs {
   float scale;
   float2* row;   // optional: row[x] = W(P1, x) (the mu numerator), P1 = (iP, jP); nullptr = none
   int iP, jP;
+  GradEpi gr;    // W_GRAD only
 };
 
 // What pass B stores of the propagated CSDA: nothing (S and the optional row only), the
-// conjugated column as the contiguous row (Hermitian CSDA), or every element at its own place.
-enum WStore { W_NONE = 0, W_HERM = 1, W_GENERAL = 2 };
+// conjugated column as the contiguous row (Hermitian CSDA), every element at its own place, or
+// (W_GRAD) nothing but the GSM parameter-gradient sums of the adjoint.
+enum WStore { W_NONE = 0, W_HERM = 1, W_GENERAL = 2, W_GRAD = 3 };
+
+// Per-thread FP32 sums of the W_GRAD epilogue for one column x2 = (c, d).
+struct GradSums {
+  float sS = 0.f, sM = 0.f, sA = 0.f;
+  // the output value R(x1, x2) at x1 = (a, b), x2 = (c, d); N / 2 = M
+  __device__ __forceinline__ void add(const GradEpi& g, int N, int a, int b, int c, int d, float2 w) {
+    if (g.qff) w = cmul(w, cmul(cmul(__ldg(g.qff + a), __ldg(g.qff + b)), cconj(cmul(__ldg(g.qff + c), __ldg(g.qff + d)))));
+    float t = w.x * __ldg(g.gtab + a * N + c) * __ldg(g.gtab + b * N + d);
+    if (g.amask) t *= __ldg(g.amask + a * N + b);
+    const int M = N / 2;
+    const float r2 = (float)((a - M) * (a - M) + (M - b) * (M - b) + (c - M) * (c - M) + (M - d) * (M - d));
+    const float dx2 = (float)((a - c) * (a - c) + (b - d) * (b - d));
+    sS = fmaf(t, r2, sS);
+    sM = fmaf(t, dx2, sM);
+    sA += t;
+  }
+};
+
+// Block reduction of the W_GRAD sums of column cd (red: 4 x 32 doubles of shared memory); writes
+// part[cd] and gmask[cd].  Every thread of the block must call it.
+__device__ __forceinline__ void grad_reduce(const GradEpi& g, int N, int cd, const GradSums& s, double* red) {
+  const float a2 = g.amask ? __ldg(g.amask + cd) : 1.f;
+  double v[4] = {(double)s.sS * a2 * g.d2, (double)s.sM * a2 * g.d2, (double)s.sA * a2, (double)s.sA};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k * 32 + warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+    for (int w = 0; w < nw; ++w) x += red[threadIdx.x * 32 + w];
+    if (threadIdx.x < 3) g.part[(size_t)cd * 3 + threadIdx.x] = x;
+    else if (g.gmask) g.gmask[cd] = (float)(g.gscale * x);
+  }
+  __syncthreads();
+}
 
 // Pass B, persistent: CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x + k gridDim.x.
 // Per slice: gather V(., ., c', d') + DFT along a (lanes along b), DFT along b with the
@@ -259,6 +353,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
   float2* buf = smem;
   float2* tw = buf + N * P;
   float2* eo = tw + N;
+  double* red = reinterpret_cast<double*>(eo + N);  // W_GRAD: block reduction
   for (int i = threadIdx.x; i < N; i += NT) {
     tw[i] = p.tw[i];
     eo[i] = p.Eout[i];
@@ -305,6 +400,15 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
         bulk_store(p.W + (size_t)cd * NN, buf, (unsigned)(NN * sizeof(float2)));
         bulk_commit();
       }
+    } else if constexpr (WST == W_GRAD) {
+      GradSums gs;
+      const GradEpi& ge = p.gr;
+      auto epi = [&](int a, int b, float2 y) {
+        const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
+        gs.add(ge, N, a, b, c, d, w);
+      };
+      fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, NoMid{}, epi);
+      grad_reduce(ge, N, cd, gs, red);
     } else {
       float2* W = p.W;
       auto epi = [=](int a, int b, float2 y) {

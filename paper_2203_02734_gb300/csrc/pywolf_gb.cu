@@ -47,7 +47,8 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 // complex values (masks, uploaded arrays, mu) or floats (S, diagonals).
 bool aligned(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; }
 
-enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3, SRC_DIAGONAL = 4 };
+// SRC_ADJOINT: the adjoint source of a loss on S and mu, set only inside the adjoint calls.
+enum SourceKind { SRC_NONE = 0, SRC_GSM = 1, SRC_ARRAY = 2, SRC_PROPAGATED = 3, SRC_DIAGONAL = 4, SRC_ADJOINT = 5 };
 
 }  // namespace
 
@@ -86,6 +87,19 @@ struct pw_csd {
   float2* Ein;    // per-axis input factors
   float* S;       // S of the last propagated plane (pass-B epilogue)
   int* err;       // device flag: a bounded wait in a kernel gave up
+  // adjoint scratch (O(N^2)): the adjoint source (diagonal, P1 row), per-column gradient sums, the
+  // GSM factor and far-field factors of the source grid, and a spare gradient triple
+  float* adj_d;
+  float2* adj_c;
+  double* gpart;
+  float* gtab;
+  float2* qtab;
+  double* g3tmp;
+  // the adjoint source of the next propagation (kind == SRC_ADJOINT)
+  int adj_herm;     // Hermitian part (row and column of P1) or the general array (row only)
+  int adj_mu;       // the source has a P1 row (a mu term)
+  int adj_iP, adj_jP;
+  const pw::GradEpi* adj_grad;  // non-null: reduce the GSM parameter gradients in pass B (W_GRAD)
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
   int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
@@ -110,7 +124,10 @@ bool supported(int N) {
 
 size_t table_bytes(int N) {
   const size_t NN = (size_t)N * N;
-  return NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 3 + 1024 + 256;
+  const size_t base = NN * sizeof(float2) * 2 + NN * sizeof(float) * 2 + (size_t)N * sizeof(float2) * 3 + 1024 + 256;
+  const size_t adj = NN * (sizeof(float) + sizeof(float2) + 3 * sizeof(double) + sizeof(float)) +
+                     (size_t)N * sizeof(float2) + 3 * sizeof(double) + 6 * 256;
+  return base + adj;
 }
 
 int num_sms() {
@@ -333,17 +350,25 @@ cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const
 }
 
 // ev: nullptr or three events recorded before pass A, between the passes and after pass B.
+// grad: pass B reduces the GSM parameter gradients of an adjoint propagation (W_GRAD) instead of
+// storing W.
 template <int N>
-cudaError_t launch_passes(int src, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+cudaError_t launch_passes(int src, bool herm, bool grad, const CUtensorMap& vmap, const pw::PassAArgs& a,
                           const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
   if (src == pw::SRC_GSM) e = launch_a_mode<N, pw::SRC_GSM>(vmap, a, x, s);
   else if (src == pw::SRC_DIAG) e = launch_a_mode<N, pw::SRC_DIAG>(vmap, a, x, s);
+  else if (src == pw::SRC_ADJ) e = launch_a_mode<N, pw::SRC_ADJ>(vmap, a, x, s);
   else e = launch_a_mode<N, pw::SRC_ARRAY>(vmap, a, x, s);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
-  if constexpr (N == 128) {
+  if (grad) {
+    if constexpr (N == 128) e = launch_b_r128<pw::W_GRAD>(b, s);
+    else if constexpr (N == 96) e = launch_b_r96<pw::W_GRAD>(b, s);
+    else if constexpr (N == 256) e = cudaErrorNotSupported;
+    else e = launch_b<N, pw::W_GRAD>(b, s);
+  } else if constexpr (N == 128) {
     e = herm ? launch_b_r128<pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
   } else if constexpr (N == 96) {
     e = herm ? launch_b_r96<pw::W_HERM>(b, s) : launch_b<N, pw::W_GENERAL>(b, s);
@@ -357,12 +382,12 @@ cudaError_t launch_passes(int src, bool herm, const CUtensorMap& vmap, const pw:
   return cudaSuccess;
 }
 
-cudaError_t dispatch(int N, int src, bool herm, const CUtensorMap& vmap, const pw::PassAArgs& a,
+cudaError_t dispatch(int N, int src, bool herm, bool grad, const CUtensorMap& vmap, const pw::PassAArgs& a,
                      const pw::PassBArgs& b, const R128Extra& x, cudaStream_t s, cudaEvent_t* ev) {
   switch (N) {
 #define PW_CASE(NN) \
   case NN:          \
-    return launch_passes<NN>(src, herm, vmap, a, b, x, s, ev);
+    return launch_passes<NN>(src, herm, grad, vmap, a, b, x, s, ev);
     PW_CASE(2) PW_CASE(4) PW_CASE(6) PW_CASE(8) PW_CASE(12) PW_CASE(16) PW_CASE(24)
     PW_CASE(32) PW_CASE(48) PW_CASE(64) PW_CASE(96) PW_CASE(128) PW_CASE(256)
 #undef PW_CASE
@@ -562,7 +587,16 @@ pw_status propagate_stream(pw_csd* h, double z, bool farfield, bool herm) {
   if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
   if (ev && (e = cudaEventRecord(ev[0], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
   pw::stream::GenArgs g{};
-  g.src = h->kind == SRC_GSM ? pw::SRC_GSM : (h->kind == SRC_DIAGONAL ? pw::SRC_DIAG : pw::SRC_ARRAY);
+  g.src = h->kind == SRC_GSM ? pw::SRC_GSM
+          : h->kind == SRC_DIAGONAL ? pw::SRC_DIAG
+          : h->kind == SRC_ADJOINT ? pw::SRC_ADJ : pw::SRC_ARRAY;
+  if (h->kind == SRC_ADJOINT) {
+    g.adj.diag = h->adj_d;
+    g.adj.cross = h->adj_mu ? h->adj_c : nullptr;
+    g.adj.iP = h->adj_iP;
+    g.adj.jP = h->adj_jP;
+    g.adj.herm = h->adj_herm;
+  }
   g.F = h->F;
   g.G = h->G;
   g.W0 = reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0);
@@ -603,7 +637,9 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (!h) return fail(PW_EINVAL, "null handle");
   if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
   if (h->kind == SRC_NONE) return fail(PW_ESTATE, "no source set for the current plane");
-  const bool herm = h->kind == SRC_GSM || h->kind == SRC_DIAGONAL || h->hermitian != 0;
+  const bool herm = h->kind == SRC_GSM || h->kind == SRC_DIAGONAL || (h->kind == SRC_ADJOINT ? h->adj_herm != 0 : h->hermitian != 0);
+  if (h->kind == SRC_ADJOINT && (h->Nz > 0 || !supported(h->N)))
+    return fail(PW_EUNSUPPORTED, "the adjoint propagation needs an unpadded grid with an FFT plan");
   if (h->Nz > 0 || !supported(h->N)) return propagate_dense(h, z, farfield, herm);
   // N = 256: the cluster engine (d256.cuh) stores point-1 rows as the conjugate of point-2 columns,
   // which needs a Hermitian CSDA; other sources take the four streaming passes (stream.cuh,
@@ -617,7 +653,9 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
     return fail(PW_EUNSUPPORTED, "the tensor-core first stage is built for Gaussian Schell-model sources only");
   pw_status st = build_tables(h, z, farfield);
   if (st != PW_OK) return st;
-  const int src = h->kind == SRC_GSM ? pw::SRC_GSM : (h->kind == SRC_DIAGONAL ? pw::SRC_DIAG : pw::SRC_ARRAY);
+  const int src = h->kind == SRC_GSM ? pw::SRC_GSM
+                  : h->kind == SRC_DIAGONAL ? pw::SRC_DIAG
+                  : h->kind == SRC_ADJOINT ? pw::SRC_ADJ : pw::SRC_ARRAY;
   pw::PassAArgs a{};
   a.F = h->F;
   a.G = h->G;
@@ -625,6 +663,14 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   a.W0 = src == pw::SRC_ARRAY ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
   a.diag = h->diag;
   a.A = (float)h->A;
+  if (src == pw::SRC_ADJ) {
+    a.diag = h->adj_d;
+    a.cross = h->adj_mu ? h->adj_c : nullptr;
+    a.iP = h->adj_iP;
+    a.jP = h->adj_jP;
+    a.herm = h->adj_herm;
+    a.A = 1.0f;
+  }
   pw::PassBArgs b{};
   b.V = reinterpret_cast<const float2*>(h->work);
   b.tw = h->tw;
@@ -646,7 +692,9 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
     const double thr = rp * rp;  // the FP64 threshold of the table kernel; r^2 is an integer
     x.ap_ithr = thr >= 2147483647.0 ? 2147483647 : (int)std::floor(thr);
   }
-  cudaError_t e = dispatch(h->N, src, herm, h->vmap, a, b, x, h->stream, ev);
+  const bool grad = src == pw::SRC_ADJ && h->adj_grad != nullptr;
+  if (grad) b.gr = *h->adj_grad;
+  cudaError_t e = dispatch(h->N, src, herm, grad, h->vmap, a, b, x, h->stream, ev);
   if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
   // The output plane becomes the current plane; its CSDA is in W, its masks are unset.
   h->d = lz / (h->N * h->d);
@@ -811,6 +859,18 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
   h->Ein = reinterpret_cast<float2*>(p);
   p += N * sizeof(float2);
   h->err = reinterpret_cast<int*>(p);
+  p += 256;
+  auto carve = [&](size_t bytes) {
+    char* q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  h->adj_d = reinterpret_cast<float*>(carve(NN * sizeof(float)));
+  h->adj_c = reinterpret_cast<float2*>(carve(NN * sizeof(float2)));
+  h->gpart = reinterpret_cast<double*>(carve(NN * 3 * sizeof(double)));
+  h->gtab = reinterpret_cast<float*>(carve(NN * sizeof(float)));
+  h->qtab = reinterpret_cast<float2*>(carve((size_t)N * sizeof(float2)));
+  h->g3tmp = reinterpret_cast<double*>(carve(3 * sizeof(double)));
   e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) {
     cudaFree(h->tables);
@@ -1072,6 +1132,142 @@ pw_status pw_gsm_gradient(pw_csd* h, double sigma_S_m, double sigma_mu_m, double
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction launch");
   return PW_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The adjoint of one propagation (Fresnel or far field over z) for a loss on S and mu of its
+// output plane; the handle's current plane is that output plane.  See pw_propagate_fresnel_adjoint.
+pw_status adjoint(pw_csd* h, double z, bool farfield, const pw_adjoint* a) {
+  if (!h || !a) return fail(PW_EINVAL, "null argument");
+  if (!finite_pos(z)) return fail(PW_EINVAL, "propagation distance must be finite and > 0 (got %g)", z);
+  if (h->Nz > 0 || !supported(h->N))
+    return fail(PW_EUNSUPPORTED, "the adjoint propagation needs an unpadded grid with an FFT plan");
+  const int N = h->N;
+  const bool has_mu = a->dev_dmu != nullptr;
+  if (!a->dev_dS && !has_mu) return fail(PW_EINVAL, "no upstream gradient (dev_dS and dev_dmu are both null)");
+  if (has_mu) {
+    if (!a->dev_S || !a->dev_mu) return fail(PW_EINVAL, "dev_dmu needs the output plane's dev_S and dev_mu");
+    if (a->iP < 0 || a->jP < 0 || a->iP >= N || a->jP >= N)
+      return fail(PW_EINVAL, "P1 = (%d, %d) outside the %d x %d grid", a->iP, a->jP, N, N);
+  }
+  const bool params = a->dev_grad3 != nullptr || a->dev_grad_amask != nullptr;
+  if (!params && !a->grad_W0) return fail(PW_EINVAL, "no gradient requested");
+  if (params && (!finite_pos(a->sigma_S_m) || !finite_pos(a->sigma_mu_m) || !std::isfinite(a->amplitude)))
+    return fail(PW_EINVAL, "the GSM parameters must be finite (sigma_S, sigma_mu > 0)");
+  if ((a->dev_dS && !aligned(a->dev_dS, 4)) || (a->dev_S && !aligned(a->dev_S, 4)) ||
+      (a->dev_amask && !aligned(a->dev_amask, 4)) || (a->dev_grad_amask && !aligned(a->dev_grad_amask, 4)) ||
+      (a->dev_dmu && !aligned(a->dev_dmu, 8)) || (a->dev_mu && !aligned(a->dev_mu, 8)) ||
+      (a->dev_grad3 && !aligned(a->dev_grad3, 8)))
+    return fail(PW_EINVAL, "misaligned device pointer");
+  const double dx = h->d, lam = h->lambda, d = lam * z / (N * dx);
+  const double c = std::pow(d / dx, 4);
+  cudaStream_t st = h->stream;
+
+  // the (conjugated) adjoint source on the output plane
+  pw::AdjPrepArgs pa{};
+  pa.N = N;
+  pa.iP = a->iP;
+  pa.jP = a->jP;
+  pa.gS = a->dev_dS;
+  pa.gmu = reinterpret_cast<const float2*>(a->dev_dmu);
+  pa.S = a->dev_S;
+  pa.mu = reinterpret_cast<const float2*>(a->dev_mu);
+  pa.d = h->adj_d;
+  pa.cross = h->adj_c;
+  pw::adjoint_prep_kernel<<<1, 1024, 0, st>>>(pa);
+  // the GSM factor (parameter gradients) and the far-field factors of the source grid
+  pw::GradArgs g{};
+  g.N = N;
+  g.d = d;
+  g.sigma_S = params ? a->sigma_S_m : 0.0;
+  g.sigma_mu = params ? a->sigma_mu_m : 0.0;
+  g.A = a->amplitude;
+  g.amask = a->dev_amask;
+  g.R = reinterpret_cast<const float2*>(h->W);
+  g.c = c;
+  g.farfield = farfield ? 1 : 0;
+  g.Kq = d * d / (2.0 * lam * z);
+  g.part = h->gpart;
+  g.gtab = h->gtab;
+  g.qtab = h->qtab;
+  g.g3 = a->dev_grad3 ? a->dev_grad3 : h->g3tmp;
+  g.gmask = a->dev_grad_amask;
+  pw::gsm_gradient_tables<<<(N * N + 255) / 256, 256, 0, st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up launch");
+
+  // one adjoint propagation: a Fresnel propagation over z from the output sampling dx of the
+  // conjugated source (back onto the source grid d)
+  auto run = [&](bool herm, const pw::GradEpi* epi) -> pw_status {
+    h->d = dx;
+    h->kind = SRC_ADJOINT;
+    h->adj_herm = herm ? 1 : 0;
+    h->adj_mu = has_mu ? 1 : 0;
+    h->adj_iP = a->iP;
+    h->adj_jP = a->jP;
+    h->adj_grad = epi;
+    pw_status r = propagate(h, z, false);
+    h->adj_grad = nullptr;
+    return r;
+  };
+  bool R_herm_in_W = false;
+  pw_status r = PW_OK;
+  if (params) {
+    // the Hermitian part of the source suffices: dW0/dtheta is Hermitian
+    if (N != 256) {
+      pw::GradEpi ge{};
+      ge.gtab = h->gtab;
+      ge.amask = a->dev_amask;
+      ge.qff = farfield ? h->qtab : nullptr;
+      ge.part = h->gpart;
+      ge.gmask = a->dev_grad_amask;
+      ge.gscale = (float)(4.0 * c * a->amplitude);
+      ge.d2 = (float)(d * d);
+      r = run(true, &ge);
+    } else {
+      r = run(true, nullptr);  // R stored in W, then the standalone gradient kernel
+      if (r == PW_OK) {
+        const size_t sh = 2 * N * sizeof(float) + 2 * N * sizeof(float2) + 32 * sizeof(double) + 64;
+        if (farfield) pw::gsm_gradient_kernel<true><<<N * N, 256, sh, st>>>(g);
+        else pw::gsm_gradient_kernel<false><<<N * N, 256, sh, st>>>(g);
+        R_herm_in_W = true;
+      }
+    }
+    if (r == PW_OK) pw::gsm_gradient_reduce<<<1, 256, 0, st>>>(g);
+  }
+  if (r == PW_OK && a->grad_W0) {
+    // a general complex W0: the whole adjoint (the P1 row without its mirrored column)
+    if (!(R_herm_in_W && !has_mu)) r = run(!has_mu, nullptr);
+    if (r == PW_OK) {
+      const int blocks = num_sms() * 8;
+      pw::w0_gradient_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<float2*>(h->W), N, (float)(2.0 * c),
+                                                     farfield ? h->qtab : nullptr);
+    }
+  }
+  if (r == PW_OK && (e = cudaGetLastError()) != cudaSuccess) r = cuda_fail(e, "adjoint kernel launch");
+  // the handle is at the source plane, with no source recorded
+  h->d = d;
+  h->kind = SRC_NONE;
+  h->W0 = nullptr;
+  h->diag = nullptr;
+  return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+pw_status pw_propagate_fresnel_adjoint(pw_csd* h, double z_m, const pw_adjoint* a) {
+  g_err.clear();
+  return adjoint(h, z_m, false, a);
+}
+
+pw_status pw_propagate_farfield_adjoint(pw_csd* h, double z_m, const pw_adjoint* a) {
+  g_err.clear();
+  return adjoint(h, z_m, true, a);
 }
 
 pw_status pw_propagate_fresnel(pw_csd* h, double z_m) {

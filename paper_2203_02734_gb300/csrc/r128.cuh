@@ -147,9 +147,11 @@ __global__ void __launch_bounds__(NT, 1)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
-    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM || SRC == SRC_ADJ) s_ab = cscale(s_ab, p.A);
     if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    AdjSlice adj{};
+    if (SRC == SRC_ADJ) adj = adj_slice(p, ab, N);
     float2 ed[4];  // Ein(d) G(b, d)
 #pragma unroll
     for (int rq = 0; rq < 4; ++rq) {
@@ -167,6 +169,7 @@ __global__ void __launch_bounds__(NT, 1)
         float2 x = cmul(sc, ed[rq]);
         if (MASK) x = cmul(x, __ldg(mask + c * N + d));
         if (ARRAY) x = cmul(x, __ldg(W0 + c * N + d));
+        if (SRC == SRC_ADJ) x = cmul(x, adj.at(p.cross, c * N + d));
         bool keep = (inmask >> (rp * 4 + rq)) & 1u;
         if (DIAG) keep = keep && c == a && d == b;
         v[rp][rq] = keep ? x : make_float2(0.f, 0.f);
@@ -308,7 +311,7 @@ __device__ __forceinline__ void stages_23_half(float2 (&v)[8][4], float2 (&w3)[2
 
 constexpr size_t kStageBytes = (size_t)N * N * sizeof(float2);  // prefetched stage-1 inputs
 constexpr size_t kXBytes = (size_t)N * N * sizeof(float2) / 2;     // half-size exchange buffer
-constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(float2); }
+constexpr size_t pass_b_smem() { return kStageBytes + kXBytes + 2 * N * sizeof(float2) + 4 * 32 * sizeof(double); }
 
 // Pass B at N = 128, persistent.  CTA blockIdx.x handles point-2 output pairs cd = blockIdx.x +
 // k gridDim.x.  Every thread gathers exactly the 32 points (a, b) = (warp + 16 rp, lane + 32 rq)
@@ -326,6 +329,7 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
   float2* xb = stg + N * N;
   float2* tw = xb + N * N / 2;
   float2* eo = tw + N;
+  double* red = reinterpret_cast<double*>(eo + N);  // W_GRAD: block reduction
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int g = vgroup<N>();
   for (int i = t; i < N; i += NT) {
@@ -373,6 +377,7 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
     float2* Wrow = p.W + (size_t)cd * N * N;
     float2* rw = p.row;
     const int iP = p.iP, jP = p.jP;
+    GradSums gs;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
 #pragma unroll
@@ -383,12 +388,17 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
         for (int rq = 0; rq < 4; ++rq) {
           const int b = lane + 32 * rq;
           const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
+          if (WST == W_GRAD) {
+            gs.add(p.gr, N, a, b, c, d, w);
+            continue;
+          }
           if (a == c && b == d) p.S[cd] = w.x;
           if (ROW && a == iP && b == jP) rw[cd] = w;
           if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
         }
       }
     }
+    if (WST == W_GRAD) grad_reduce(p.gr, N, cd, gs, red);
   }
   cp_async_wait_all();
 }

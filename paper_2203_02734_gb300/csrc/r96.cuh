@@ -153,9 +153,11 @@ __global__ void __launch_bounds__(NT, 2)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
-    if (SRC == SRC_GSM) s_ab = cscale(s_ab, p.A);
+    if (SRC == SRC_GSM || SRC == SRC_ADJ) s_ab = cscale(s_ab, p.A);
     if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
     const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    AdjSlice adj{};
+    if (SRC == SRC_ADJ) adj = adj_slice(p, ab, N);
     float2 ed[3];  // Ein(d) G(b, d)
 #pragma unroll
     for (int kq = 0; kq < 3; ++kq) {
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(NT, 2)
           float2 x = cmul(sc, ed[kq]);
           if (MASK) x = cmul(x, __ldg(mask + c * N + d));
           if (ARRAY) x = cmul(x, __ldg(W0 + c * N + d));
+          if (SRC == SRC_ADJ) x = cmul(x, adj.at(p.cross, c * N + d));
           bool keep = (inmask >> (i * 24 + kp * 3 + kq)) & 1ull;
           if (DIAG) keep = keep && c == a && d == b;
           v[i][kp][kq] = keep ? x : make_float2(0.f, 0.f);
@@ -203,7 +206,9 @@ __global__ void __launch_bounds__(NT, 2)
 }
 
 constexpr size_t pass_a_smem() { return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float); }
-constexpr size_t pass_b_smem() { return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2); }
+constexpr size_t pass_b_smem() {
+  return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2) + 4 * 32 * sizeof(double);
+}
 
 // Pass B at N = 96, persistent (two CTAs per SM).  CTA blockIdx.x handles point-2 output pairs
 // cd = blockIdx.x + k gridDim.x: every thread loads its 48 stage-1 inputs of the strided column
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(NT, 2) pass_b_r96(PassBArgs p) {
   float2* X = smem;
   float2* tw = X + N * P;
   float2* eo = tw + N;
+  double* red = reinterpret_cast<double*>(eo + N);  // W_GRAD: block reduction
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int g = vgroup<N>();
   constexpr size_t NN = (size_t)N * N;
@@ -254,6 +260,7 @@ __global__ void __launch_bounds__(NT, 2) pass_b_r96(PassBArgs p) {
     stages<+1>(v, w3, X, tw);
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
     float2* Wrow = p.W + (size_t)cd * NN;
+    GradSums gs;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int u = t + NT * i, jq = u % 24, jp = u / 24;
@@ -265,12 +272,17 @@ __global__ void __launch_bounds__(NT, 2) pass_b_r96(PassBArgs p) {
         for (int kq = 0; kq < 4; ++kq) {
           const int b = jq + 24 * kq;
           const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][kp][kq]);
+          if (WST == W_GRAD) {
+            gs.add(p.gr, N, a, b, c, d, w);
+            continue;
+          }
           if (a == c && b == d) p.S[cd] = w.x;
           if (ROW && a == iP && b == jP) rw[cd] = w;
           if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
         }
       }
     }
+    if (WST == W_GRAD) grad_reduce(p.gr, N, cd, gs, red);
   }
 }
 

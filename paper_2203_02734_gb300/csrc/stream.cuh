@@ -60,11 +60,12 @@ __device__ __forceinline__ void stage2(const float2* X, int l, int k2, float2 (&
 }
 
 struct GenArgs {
-  int src;             // SRC_GSM, SRC_ARRAY, SRC_DIAG
+  int src;             // SRC_GSM, SRC_ARRAY, SRC_DIAG, SRC_ADJ
   const float2* F;     // N x N input factor (propagator, checkerboard, aperture, lens, mask)
   const float* G;      // GSM axis factor
   const float2* W0;    // uploaded CSDA (SRC_ARRAY)
-  const float* diag;   // N x N diagonal (SRC_DIAG)
+  const float* diag;   // N x N diagonal (SRC_DIAG, SRC_ADJ)
+  PassAArgs adj;       // SRC_ADJ: diag, cross, P1, herm (the other fields unused)
   float A;
   const float2* tw;    // exp(-2 pi i m / N)
   float2* out;         // N^4, natural layout
@@ -81,6 +82,8 @@ __global__ void __launch_bounds__(NT) gen_d_kernel(GenArgs g) {
     const size_t r0 = tile * L;
     const int ab = (int)(r0 / N), a = ab / N, b = ab % N, c0 = (int)(r0 % N);
     const float2 fab = cconj(g.F[ab]);
+    AdjSlice adj{};
+    if (g.src == SRC_ADJ) adj = adj_slice(g.adj, ab, N);
     __syncthreads();  // the previous tile's stage 2 has read X; tw is written
     // generate: thread t -> d = t, all 16 rows (c = c0 + l) of the tile
     const int d = t;
@@ -93,6 +96,8 @@ __global__ void __launch_bounds__(NT) gen_d_kernel(GenArgs g) {
         v = cscale(f, g.A * g.G[a * N + c] * g.G[b * N + d]);
       } else if (g.src == SRC_ARRAY) {
         v = cmul(f, g.W0[(r0 + ll) * N + d]);
+      } else if (g.src == SRC_ADJ) {
+        v = cmul(cscale(f, g.A), adj.at(g.adj.cross, c * N + d));
       } else {
         v = (a == c && b == d) ? cscale(f, g.A * g.diag[ab]) : make_float2(0.f, 0.f);
       }

@@ -97,11 +97,13 @@ def record(name, **errs):
 # about 1e-7 max|W| everywhere, so mu = W(P1,x)/sqrt(S(P1) S(x)) carries an error of about
 # 1e-7 / sqrt(S(x)/max S): 1e-5 needs S(x)/max S >= ~1e-4.
 MU_REGION = 1e-4
-# In the wider region S(x) >= 1e-6 max S the same model gives ~1e-4 per point at the region's
-# edge; the rel-L2 over the region is dominated by the brighter points.  It is asserted against
-# a stated bound so that a regression there is caught.
+# In the wider region S(x) >= 1e-6 max S the same model gives eps / sqrt(1e-6) = 1e-4 per point at
+# the region's edge (eps ~ 1e-7, the FP32 error of W relative to max |W|); the rel-L2 over the
+# region is at most that edge error when the dim points dominate it (measured: 1.5e-5 on the GSM
+# workloads, 1.4e-4 on a random three-mode CSDA at N = 16).  It is asserted against 3e-4, three
+# times the model's edge error, so that a regression of the FP32 error there is caught.
 MU_WIDE_REGION = 1e-6
-MU_WIDE_BOUND = 5e-5
+MU_WIDE_BOUND = 3e-4
 
 
 def check_s_mu(out, Wref, P1, tol=1e-5, name=None):

@@ -1,5 +1,8 @@
 """The hand-written adjoint (GPU) against the FP64 oracle's adjoint gradient, which is itself
-pinned by central finite differences (tests/test_oracle_pins.py); and a short fit."""
+pinned by central finite differences (tests/test_oracle_pins.py): losses on S alone and on S and
+mu together, gradients in the GSM parameters and the amplitude mask (reduced in the adjoint's
+second pass) and in an uploaded W0 (stored); the C entry point's argument checks; and a short
+fit."""
 import numpy as np
 import pytest
 
@@ -76,3 +79,115 @@ def test_fit_decreases_loss():
         losses.append(float(L))
     model.close()
     assert losses[-1] < 0.2 * losses[0], losses
+
+
+def _sm_targets(N, seed):
+    S_t = 1e-3 * (0.5 + WL.uniform01(seed, N * N).reshape(N, N))
+    mu_t = 0.3 * np.exp(2j * np.pi * WL.uniform01(seed + 1, N * N).reshape(N, N))
+    wS = 1e6 * (0.5 + WL.uniform01(seed + 2, N * N).reshape(N, N))
+    wmu = 0.5 + WL.uniform01(seed + 3, N * N).reshape(N, N)
+    return S_t, wS, mu_t, wmu
+
+
+def _torch_loss(S, mu, S_t, wS, mu_t, wmu):
+    import torch
+    t = lambda x: torch.tensor(x, device="cuda")  # noqa: E731
+    return torch.sum(t(wS) * (S.double() - t(S_t)) ** 2) + torch.sum(t(wmu) * torch.abs(mu.cdouble() - t(mu_t)) ** 2)
+
+
+@pytest.mark.parametrize("N,z,farfield", [(16, 0.6, False), (16, 0.6, True), (32, 1.0, False), (64, 0.8, True)])
+def test_s_and_mu_loss_gradient_matches_oracle(N, z, farfield):
+    """A loss on S and mu(P1, .): the single adjoint call's parameter and mask gradients against the
+    oracle's adjoint (reading R22), 1e-4 relative."""
+    import torch
+    from paper_2203_02734_gb300.autograd import GSMPropagation
+    P1 = (N // 2 - 1, N // 2 + 2)
+    amask = WL.to_c64(WL.amplitude_mask(N, seed=N)).real.astype(np.float64)
+    S_t, wS, mu_t, wmu = _sm_targets(N, 300 + N)
+    model = GSMPropagation(N, DXI, LAM, z, P1=P1, farfield=farfield)
+    sS = torch.tensor(SS, dtype=torch.float64, requires_grad=True)
+    sM = torch.tensor(SM, dtype=torch.float64, requires_grad=True)
+    A = torch.tensor(1.2, dtype=torch.float64, requires_grad=True)
+    am = torch.tensor(amask, dtype=torch.float32, device="cuda", requires_grad=True)
+    S, mu = model(sS, sM, A, am)
+    L = _torch_loss(S, mu, S_t, wS, mu_t, wmu)
+    L.backward()
+    model.close()
+    ref = O.sm_loss_gradient(SS, SM, 1.2, amask, N, DXI, LAM, z, P1, S_t, wS, mu_t, wmu, farfield)
+    from gpu_cases import record
+    got = (float(sS.grad), float(sM.grad), float(A.grad))
+    errs = [abs(got[k] - ref[1 + k]) / abs(ref[1 + k]) for k in range(3)]
+    emask = np.linalg.norm(am.grad.cpu().numpy() - ref[4]) / np.linalg.norm(ref[4])
+    record("sm_grad_n%d_%s" % (N, "ff" if farfield else "fr"), sigma_S=errs[0], sigma_mu=errs[1], A=errs[2],
+           mask=emask)
+    assert abs(float(L) / ref[0] - 1) < 1e-4
+    assert max(errs) < 1e-4, errs
+    assert emask < 1e-4, emask
+
+
+@pytest.mark.parametrize("with_mu", [False, True], ids=["S_loss", "S_and_mu_loss"])
+@pytest.mark.parametrize("farfield", [False, True])
+def test_w0_gradient_matches_oracle(with_mu, farfield):
+    """dL/dRe W0 + i dL/dIm W0 of an uploaded Hermitian W0 (N = 16): the adjoint stored by the single
+    call (Hermitian for an S-loss; the general, non-Hermitian adjoint with a mu term) against the
+    oracle's 2 P^H(dL/dW_B*), element by element."""
+    import torch
+    from paper_2203_02734_gb300.autograd import CSDPropagation
+    N, z = 16, 0.45
+    P1 = (7, 9)
+    R = WL.random_csd(N, seed=21, n_modes=3)
+    W0 = (O.gsm_source(N, DXI, SS, SM) + 0.1 * R / np.abs(R).max()).astype(np.complex64)
+    S_t, wS, mu_t, wmu = _sm_targets(N, 500)
+    if not with_mu:
+        wmu = np.zeros_like(wmu)
+    model = CSDPropagation(N, DXI, LAM, z, P1=P1, farfield=farfield)
+    W0t = torch.tensor(W0, device="cuda", requires_grad=True)
+    S, mu = model(W0t)
+    L = torch.sum(torch.tensor(wS, device="cuda") * (S.double() - torch.tensor(S_t, device="cuda")) ** 2)
+    if with_mu:
+        L = L + torch.sum(torch.tensor(wmu, device="cuda") * torch.abs(mu.cdouble() - torch.tensor(mu_t, device="cuda")) ** 2)
+    L.backward()
+    g = W0t.grad.cpu().numpy().astype(np.complex128)
+    model.close()
+    W064 = W0.astype(np.complex128)
+    L0, WB, S0, mu0 = O.sm_loss(W064, DXI, LAM, z, P1, S_t, wS, mu_t, wmu, farfield)
+    Y = O.adjoint_source(WB, P1, 2.0 * wS * (S0 - S_t), 2.0 * wmu * (mu0 - mu_t))
+    gref = 2.0 * O.propagate_adjoint(Y, DXI, LAM, z, farfield)
+    e = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    from gpu_cases import record
+    record("w0_grad_%s_%s" % ("smu" if with_mu else "s", "ff" if farfield else "fr"), W0grad=e)
+    assert abs(float(L) / L0 - 1) < 1e-4
+    assert e < 1e-4, e
+    # with a mu term the gradient is not Hermitian (the P1 row has no mirrored column)
+    M = gref.reshape(N * N, N * N)
+    herm = np.linalg.norm(M - M.conj().T) / np.linalg.norm(M)
+    assert (herm > 1e-3) == with_mu
+
+
+def test_adjoint_entry_point_rejects_bad_arguments():
+    import torch
+    import paper_2203_02734_gb300 as pw
+    N = 16
+    c = pw.CSD(N, DXI, LAM)
+    g3 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    dS = torch.zeros((N, N), dtype=torch.float32, device="cuda")
+    dmu = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+
+    def call(**kw):
+        a = pw.pw_adjoint()
+        a.sigma_S_m, a.sigma_mu_m, a.amplitude = SS, SM, 1.0
+        for k, v in kw.items():
+            setattr(a, k, v)
+        with pytest.raises(pw.PwError) as e:
+            pw.pw_propagate_fresnel_adjoint(c.h, 0.5, a)
+        return str(e.value)
+    assert "no upstream gradient" in call(dev_grad3=g3.data_ptr())
+    assert "no gradient requested" in call(dev_dS=dS.data_ptr())
+    assert "needs the output plane" in call(dev_dmu=dmu.data_ptr(), dev_grad3=g3.data_ptr())
+    assert "outside" in call(dev_dmu=dmu.data_ptr(), dev_S=dS.data_ptr(), dev_mu=dmu.data_ptr(), iP=N,
+                             dev_grad3=g3.data_ptr())
+    assert "misaligned" in call(dev_dS=dS.data_ptr() + 2, dev_grad3=g3.data_ptr())
+    assert "GSM parameters" in call(dev_dS=dS.data_ptr(), dev_grad3=g3.data_ptr(), sigma_S_m=-1.0)
+    pw.pw_csd_set_padding(c.h, 24)
+    assert "PW_EUNSUPPORTED" in call(dev_dS=dS.data_ptr(), dev_grad3=g3.data_ptr())
+    c.close()
