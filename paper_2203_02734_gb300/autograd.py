@@ -82,6 +82,9 @@ class GSMPropagation:
 class GSMIntensity(GSMPropagation):
     """S alone of GSMPropagation (a loss on S only)."""
 
+    def __init__(self, N, dxi, lam, z, farfield=False, device=None):
+        super().__init__(N, dxi, lam, z, P1=None, farfield=farfield, device=device)
+
     def __call__(self, sigma_S, sigma_mu, A, amask):
         return _GSMFn.apply(sigma_S, sigma_mu, A, amask, self)[0]
 

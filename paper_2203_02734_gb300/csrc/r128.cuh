@@ -104,7 +104,9 @@ __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][
 // Pass A at N = 128, persistent.  Per point-1 pair (a, b): build W1(c, d) = s_ab F(c, d) G(a,c)
 // G(b,d) (or W0 x factors) in registers, 2D DFT (sign -1) over (c, d), natural-order slice into
 // shared memory, one TMA tensor store into the V layout.  F(c, d) = Ein(c) Ein(d) Y(c, d) m(c, d)
-// from the per-axis factors, the aperture test and the optional mask.
+// from the per-axis factors, the aperture test and the optional mask; the GSM factors G(a, c),
+// G(b, d) are read through L1.  Stage 3 reads and writes only its warp's rows, so the
+// natural-order write after it needs only a warp barrier.
 template <int SRC, bool MASK>
 __global__ void __launch_bounds__(NT, 1)
     pass_a_r128(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
@@ -114,8 +116,6 @@ __global__ void __launch_bounds__(NT, 1)
   float2* buf = smem;
   float2* tw = buf + N * N;
   float2* ein = tw + N;
-  float* gA = reinterpret_cast<float*>(ein + N);
-  float* gB = gA + N;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int i = t; i < N; i += NT) {
     tw[i] = p.tw[i];
@@ -134,15 +134,9 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int rq = 0; rq < 4; ++rq)
       if (inside(warp + 16 * rp, lane + 32 * rq)) inmask |= 1u << (rp * 4 + rq);
+  __syncthreads();  // tw, ein
   for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
     const int a = ab / N, b = ab - a * N;
-    if (SRC == SRC_GSM) {
-      for (int i = t; i < N; i += NT) {
-        gA[i] = p.G[a * N + i];
-        gB[i] = p.G[b * N + i];
-      }
-    }
-    __syncthreads();
     // s_ab = A conj(F(a, b)), F(i, j) = Ein(i) Ein(j) Y(i, j) m(i, j)
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
@@ -156,13 +150,13 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
     for (int rq = 0; rq < 4; ++rq) {
       const int d = lane + 32 * rq;
-      ed[rq] = SRC == SRC_GSM ? cscale(ein[d], gB[d]) : ein[d];
+      ed[rq] = SRC == SRC_GSM ? cscale(ein[d], __ldg(p.G + b * N + d)) : ein[d];
     }
     float2 v[8][4];
 #pragma unroll
     for (int rp = 0; rp < 8; ++rp) {
       const int c = warp + 16 * rp;
-      const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], gA[c])) : cmul(s_ab, ein[c]);
+      const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], __ldg(p.G + a * N + c))) : cmul(s_ab, ein[c]);
 #pragma unroll
       for (int rq = 0; rq < 4; ++rq) {
         const int d = lane + 32 * rq;
@@ -180,7 +174,7 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     float2 w3[2][4][4];
     stages_23<-1>(v, w3, buf, tw);
-    __syncthreads();
+    __syncwarp();  // stage 3 reads only the warp's own rows (c' = warp + 16 i + 32 rp)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -197,7 +191,7 @@ __global__ void __launch_bounds__(NT, 1)
   if (t == 0) bulk_wait_all();
 }
 
-constexpr size_t pass_a_smem() { return (size_t)N * N * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float); }
+constexpr size_t pass_a_smem() { return (size_t)N * N * sizeof(float2) + 2 * N * sizeof(float2); }
 
 }  // namespace r128
 }  // namespace pw
