@@ -268,6 +268,9 @@ pw_status pw_csd_get_dft_mode(const pw_csd* h, int* mode);
  * not recorded. */
 pw_status pw_csd_enable_timing(pw_csd* h, int max_props);
 pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count);
+/* The same with the engine's passes apart: at N = 256 (three streaming passes) ms_first is the
+ * first pass, ms_second and ms_third the second and third; elsewhere ms_third is 0. */
+pw_status pw_csd_pass_times3(pw_csd* h, double* ms_first, double* ms_second, double* ms_third, int* count);
 
 /* ---- Batched runs: many instances in one persistent launch --------------------------------
  * For the polychromatic case of Sec. 6 (future work in the paper: many frequencies of a

@@ -39,6 +39,7 @@ SIGNATURES = {
     "pw_csd_get_padding": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_get_dft_mode": (_i, [_vp, ctypes.POINTER(_i)]),
     "pw_csd_pass_times": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
+    "pw_csd_pass_times3": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "pw_source_gsm": (_i, [_vp, _d, _d, _d]),
     "pw_source_aperture": (_i, [_vp, _d]),
     "pw_source_lens": (_i, [_vp, _d]),
@@ -190,6 +191,13 @@ def pw_csd_pass_times(h):
     a, b, n = _d(), _d(), _i()
     _check(LIB.pw_csd_pass_times(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
     return a.value, b.value, n.value
+
+
+def pw_csd_pass_times3(h):
+    """(ms of the first pass, of the second, of the third (0 for two-pass engines), count)."""
+    a, b, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(LIB.pw_csd_pass_times3(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)))
+    return a.value, b.value, c.value, n.value
 
 
 def pw_source_gsm(h, sigma_S_m, sigma_mu_m, amplitude=1.0):

@@ -17,7 +17,7 @@
 #include "d256.cuh"
 #include "dense.cuh"
 #include "dense_tc.cuh"
-#include "stream.cuh"
+#include "t256.cuh"
 #include "grad.cuh"
 #include "r128.cuh"
 #include "r96.cuh"
@@ -101,12 +101,16 @@ struct pw_csd {
   int adj_iP, adj_jP;
   const pw::GradEpi* adj_grad;  // non-null: reduce the GSM parameter gradients in pass B (W_GRAD)
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
+  CUtensorMap ymap;  // N = 256: the second pass's tiles of Y1 (work buffer)
+  CUtensorMap wmap;  // N = 256: the third pass's tiles of W
   int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
   void* qbuf;        // split DFT matrices of the tensor-core dense path (allocated on first use)
   int stall;         // failure-detection test: chunk whose copy CTA 0 leaves out, next dense TC run only
-  // optional per-pass timing: 3 events per recorded propagation
+  // optional per-pass timing: 4 events per recorded propagation (before the first pass, after it,
+  // after the last, and between the second and third passes of the N = 256 engine)
   std::vector<cudaEvent_t> events;
+  std::vector<char> three;  // per recorded propagation: the middle event was recorded
   int timed;
 };
 
@@ -410,7 +414,40 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-pw_status make_vmap(pw_csd* h) { return pwi::encode_vmap(&h->vmap, h->work, h->N); }
+// N = 256 (three-pass engine): Y1[a][b][r][k_l][d'] in the work buffer as floats {2N, 64, 4, N, N}
+// with the second pass's box {16, 1, 4, N, 1} (8 d' x 4 r x all b), and W[a][b'][c'][d'] as floats
+// {2N, N, N, N} with the third pass's box {64, 1, 1, N} (32 d' x all a).
+pw_status make_t256_maps(pw_csd* h) {
+  auto enc = encode_tiled();
+  if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  constexpr cuuint64_t N = 256, row = 2 * N * sizeof(float);
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  {
+    cuuint64_t dims[5] = {2 * N, 64, 4, N, N};
+    cuuint64_t strides[4] = {row, row * 64, row * 64 * 4, row * 64 * 4 * N};
+    cuuint32_t box[5] = {16, 1, 4, (cuuint32_t)N, 1};
+    CUresult r = enc(&h->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->work, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (second-pass tiles) failed (CUresult %d)", (int)r);
+  }
+  {
+    cuuint64_t dims[4] = {2 * N, N, N, N};
+    cuuint64_t strides[3] = {row, row * N, row * N * N};
+    cuuint32_t box[4] = {64, 1, 1, (cuuint32_t)N};
+    CUresult r = enc(&h->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->W, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (third-pass tiles) failed (CUresult %d)", (int)r);
+  }
+  return PW_OK;
+}
+
+pw_status make_vmap(pw_csd* h) {
+  pw_status st = pwi::encode_vmap(&h->vmap, h->work, h->N);
+  if (st == PW_OK && h->N == 256) st = make_t256_maps(h);
+  return st;
+}
 
 // Fill F, M0, G, tw, Eout for a propagation over z (z <= 0: source-plane view only).
 pw_status build_tables(pw_csd* h, double z, bool farfield) {
@@ -464,7 +501,7 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   if (st != PW_OK) return st;
   const double d = h->d, lz = h->lambda * z, dx = lz / (Nz * d);
   cudaEvent_t* ev = nullptr;
-  if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
+  if (!h->events.empty() && (size_t)(4 * (h->timed + 1)) <= h->events.size()) ev = &h->events[4 * h->timed++];
   cudaError_t e = cudaSuccess;
   if (ev && (e = cudaEventRecord(ev[0], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
   pw::dense::TabArgs t{};
@@ -568,59 +605,78 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   return PW_OK;
 }
 
-// N = 256, four streaming passes (stream.cuh): the source into work with the DFT along d, DFTs
-// along c and b in place, the DFT along a with the output factors and S into W.  The first two
-// count as the first pass for the pass timing.
-pw_status propagate_stream(pw_csd* h, double z, bool farfield, bool herm) {
-  pw_status st = build_tables(h, z, farfield);
-  if (st != PW_OK) return st;
-  static int grid = 0;
+// N = 256, three streaming passes (t256.cuh): the source with the point-2 DFT over (m, d) into the
+// work buffer, the radix-4 over r and the DFT over b into W, the DFT over a with the output factors
+// and S in place in W.  Any source (Hermitian or not).  Events: the first pass, then the second and
+// third apart.
+pw_status propagate_t256(pw_csd* h, double z, bool herm) {
+  namespace T = pw::t256;
+  const int src = h->kind == SRC_GSM ? pw::SRC_GSM
+                  : h->kind == SRC_DIAGONAL ? pw::SRC_DIAG
+                  : h->kind == SRC_ADJOINT ? pw::SRC_ADJ : pw::SRC_ARRAY;
+  pw::PassAArgs a{};
+  a.F = h->F;
+  a.G = h->G;
+  a.tw = h->tw;
+  a.W0 = src == pw::SRC_ARRAY ? reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0) : nullptr;
+  a.diag = h->diag;
+  a.A = (float)h->A;
+  if (src == pw::SRC_ADJ) {
+    a.diag = h->adj_d;
+    a.cross = h->adj_mu ? h->adj_c : nullptr;
+    a.iP = h->adj_iP;
+    a.jP = h->adj_jP;
+    a.herm = h->adj_herm;
+    a.A = 1.0f;
+  }
+  pw::PassBArgs b{};
+  b.tw = h->tw;
+  b.Eout = h->Eout;
+  b.W = reinterpret_cast<float2*>(h->W);
+  b.S = h->S;
+  const double lz = h->lambda * z;
+  b.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
+  static int g2 = 0, g3 = 0;
   cudaError_t e = cudaSuccess;
-  if (grid == 0) {
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pw::stream::axis_kernel<1, true>,
-                                                           pw::stream::NT, 0)) != cudaSuccess)
-      return cuda_fail(e, "occupancy of the streaming passes");
-    grid = num_sms() * (per_sm > 0 ? per_sm : 1);
+  // one 512-thread CTA per SM; the shared-memory limit is raised once per source mode
+  auto kernel1 = [&](auto k, bool& ready) -> cudaError_t {
+    if (!ready) {
+      cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::pass1_smem());
+      if (r != cudaSuccess) return r;
+      ready = true;
+    }
+    k<<<num_sms(), T::NT1, T::pass1_smem(), h->stream>>>(a, reinterpret_cast<float2*>(h->work));
+    return cudaGetLastError();
+  };
+  static bool ready1[4] = {false, false, false, false};
+  if (g2 == 0) {
+    if ((e = cudaFuncSetAttribute(T::pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)T::pass2_smem())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(T::pass3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)T::pass3_smem())) != cudaSuccess ||
+        (e = persistent_grid(T::pass2_kernel, T::NT2, T::pass2_smem(), 1 << 30, &g2)) != cudaSuccess ||
+        (e = persistent_grid(T::pass3_kernel, T::NT2, T::pass3_smem(), 1 << 30, &g3)) != cudaSuccess)
+      return cuda_fail(e, "set-up of the N = 256 passes");
   }
   cudaEvent_t* ev = nullptr;
-  if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
-  if (ev && (e = cudaEventRecord(ev[0], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
-  pw::stream::GenArgs g{};
-  g.src = h->kind == SRC_GSM ? pw::SRC_GSM
-          : h->kind == SRC_DIAGONAL ? pw::SRC_DIAG
-          : h->kind == SRC_ADJOINT ? pw::SRC_ADJ : pw::SRC_ARRAY;
-  if (h->kind == SRC_ADJOINT) {
-    g.adj.diag = h->adj_d;
-    g.adj.cross = h->adj_mu ? h->adj_c : nullptr;
-    g.adj.iP = h->adj_iP;
-    g.adj.jP = h->adj_jP;
-    g.adj.herm = h->adj_herm;
+  if (!h->events.empty() && (size_t)(4 * (h->timed + 1)) <= h->events.size()) {
+    h->three[h->timed] = 1;
+    ev = &h->events[4 * h->timed++];
   }
-  g.F = h->F;
-  g.G = h->G;
-  g.W0 = reinterpret_cast<const float2*>(h->kind == SRC_PROPAGATED ? h->W : h->W0);
-  g.diag = h->diag;
-  g.A = (float)h->A;
-  g.tw = h->tw;
-  g.out = reinterpret_cast<float2*>(h->work);
-  pw::stream::gen_d_kernel<<<grid, pw::stream::NT, 0, h->stream>>>(g);
-  pw::stream::AxisArgs ax{};
-  ax.X = reinterpret_cast<float2*>(h->work);
-  ax.tw = h->tw;
-  ax.axis = 2;
-  pw::stream::axis_kernel<-1, false><<<grid, pw::stream::NT, 0, h->stream>>>(ax);
+  if (ev && (e = cudaEventRecord(ev[0], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  switch (src) {
+    case pw::SRC_GSM: e = kernel1(T::pass1_kernel<pw::SRC_GSM>, ready1[pw::SRC_GSM]); break;
+    case pw::SRC_DIAG: e = kernel1(T::pass1_kernel<pw::SRC_DIAG>, ready1[pw::SRC_DIAG]); break;
+    case pw::SRC_ADJ: e = kernel1(T::pass1_kernel<pw::SRC_ADJ>, ready1[pw::SRC_ADJ]); break;
+    default: e = kernel1(T::pass1_kernel<pw::SRC_ARRAY>, ready1[pw::SRC_ARRAY]); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "first-pass launch (N = 256)");
   if (ev && (e = cudaEventRecord(ev[1], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
-  ax.axis = 1;
-  pw::stream::axis_kernel<+1, false><<<grid, pw::stream::NT, 0, h->stream>>>(ax);
-  ax.axis = 0;
-  ax.out = reinterpret_cast<float2*>(h->W);
-  ax.Eout = h->Eout;
-  const double lz = h->lambda * z;
-  ax.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
-  ax.S = h->S;
-  pw::stream::axis_kernel<+1, true><<<grid, pw::stream::NT, 0, h->stream>>>(ax);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "streaming propagation launch");
+  T::pass2_kernel<<<g2, T::NT2, T::pass2_smem(), h->stream>>>(h->ymap, h->tw, reinterpret_cast<float2*>(h->W), h->err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "second-pass launch (N = 256)");
+  if (ev && (e = cudaEventRecord(ev[3], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  T::pass3_kernel<<<g3, T::NT2, T::pass3_smem(), h->stream>>>(h->wmap, b, h->err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "third-pass launch (N = 256)");
   if (ev && (e = cudaEventRecord(ev[2], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
   h->d = lz / (h->N * h->d);
   h->kind = SRC_PROPAGATED;
@@ -641,18 +697,13 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   if (h->kind == SRC_ADJOINT && (h->Nz > 0 || !supported(h->N)))
     return fail(PW_EUNSUPPORTED, "the adjoint propagation needs an unpadded grid with an FFT plan");
   if (h->Nz > 0 || !supported(h->N)) return propagate_dense(h, z, farfield, herm);
-  // N = 256: the cluster engine (d256.cuh) stores point-1 rows as the conjugate of point-2 columns,
-  // which needs a Hermitian CSDA; other sources take the four streaming passes (stream.cuh,
-  // measured 76.7 ms per step against 58.4 ms for the cluster engine on the phase-screen workload)
-  if (h->N == 256 && !herm) {
-    if (h->dft_mode == PW_DFT_TC_BF16X3)
-      return fail(PW_EUNSUPPORTED, "the tensor-core first stage is built for Gaussian Schell-model sources only");
-    return propagate_stream(h, z, farfield, herm);
-  }
   if (h->dft_mode == PW_DFT_TC_BF16X3 && h->kind != SRC_GSM)
     return fail(PW_EUNSUPPORTED, "the tensor-core first stage is built for Gaussian Schell-model sources only");
   pw_status st = build_tables(h, z, farfield);
   if (st != PW_OK) return st;
+  // N = 256: the three streaming passes (t256.cuh), any source; the cluster engine (d256.cuh) runs
+  // only the comparison mode with the tensor-core first stage
+  if (h->N == 256 && h->dft_mode != PW_DFT_TC_BF16X3) return propagate_t256(h, z, herm);
   const int src = h->kind == SRC_GSM ? pw::SRC_GSM
                   : h->kind == SRC_DIAGONAL ? pw::SRC_DIAG
                   : h->kind == SRC_ADJOINT ? pw::SRC_ADJ : pw::SRC_ARRAY;
@@ -680,7 +731,7 @@ pw_status propagate(pw_csd* h, double z, bool farfield) {
   const double lz = h->lambda * z;
   b.scale = (float)((h->d * h->d / lz) * (h->d * h->d / lz));
   cudaEvent_t* ev = nullptr;
-  if (!h->events.empty() && (size_t)(3 * (h->timed + 1)) <= h->events.size()) ev = &h->events[3 * h->timed++];
+  if (!h->events.empty() && (size_t)(4 * (h->timed + 1)) <= h->events.size()) ev = &h->events[4 * h->timed++];
   R128Extra x{};
   x.Ein = h->Ein;
   x.mask = reinterpret_cast<const float2*>(h->mask);
@@ -890,6 +941,7 @@ pw_status pw_csd_create(pw_csd** out, int N, double dxi_m, double lambda_m, pw_c
 static void free_events(pw_csd* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   h->events.clear();
+  h->three.clear();
   h->timed = 0;
 }
 
@@ -948,7 +1000,8 @@ pw_status pw_csd_enable_timing(pw_csd* h, int max_props) {
   if (!h) return fail(PW_EINVAL, "null handle");
   if (max_props < 0) return fail(PW_EINVAL, "max_props must be >= 0");
   free_events(h);
-  h->events.resize((size_t)3 * max_props);
+  h->events.resize((size_t)4 * max_props);
+  h->three.assign((size_t)max_props, 0);
   for (size_t i = 0; i < h->events.size(); ++i) {
     cudaError_t e = cudaEventCreate(&h->events[i]);
     if (e != cudaSuccess) {
@@ -960,24 +1013,41 @@ pw_status pw_csd_enable_timing(pw_csd* h, int max_props) {
   return PW_OK;
 }
 
-pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count) {
+pw_status pw_csd_pass_times3(pw_csd* h, double* ms_first, double* ms_second, double* ms_third, int* count) {
   g_err.clear();
-  if (!h || !ms_first || !ms_second || !count) return fail(PW_EINVAL, "null argument");
-  double sa = 0.0, sb = 0.0;
+  if (!h || !ms_first || !ms_second || !ms_third || !count) return fail(PW_EINVAL, "null argument");
+  double sa = 0.0, sb = 0.0, sc = 0.0;
   for (int k = 0; k < h->timed; ++k) {
-    float t1 = 0.f, t2 = 0.f;
-    cudaError_t e = cudaEventSynchronize(h->events[3 * k + 2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, h->events[3 * k], h->events[3 * k + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, h->events[3 * k + 1], h->events[3 * k + 2]);
+    cudaEvent_t* ev = &h->events[4 * k];
+    float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    cudaError_t e = cudaEventSynchronize(ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[0], ev[1]);
+    if (e == cudaSuccess) {
+      if (h->three[k]) {
+        e = cudaEventElapsedTime(&t2, ev[1], ev[3]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t3, ev[3], ev[2]);
+      } else {
+        e = cudaEventElapsedTime(&t2, ev[1], ev[2]);
+      }
+    }
     if (e != cudaSuccess) return cuda_fail(e, "pass timing events");
     sa += t1;
     sb += t2;
+    sc += t3;
   }
   *ms_first = sa;
   *ms_second = sb;
+  *ms_third = sc;
   *count = h->timed;
   h->timed = 0;
   return PW_OK;
+}
+
+pw_status pw_csd_pass_times(pw_csd* h, double* ms_first, double* ms_second, int* count) {
+  double m3 = 0.0;
+  pw_status st = pw_csd_pass_times3(h, ms_first, ms_second, &m3, count);
+  if (st == PW_OK) *ms_second += m3;
+  return st;
 }
 
 pw_status pw_csd_set_padding(pw_csd* h, int Nz) {

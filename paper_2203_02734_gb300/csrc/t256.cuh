@@ -1,0 +1,361 @@
+// t256.cuh -- the propagation at N = 256 as three streaming passes over independent tiles.
+//
+// One 256 x 256 slice (512 KB) does not fit one SM, and spreading it over a cluster makes every
+// point cross the SM-to-SM network, which on this GPU moves about 4 TB/s in all (less than HBM).
+// Here the exchange goes through HBM instead, in three passes of 8 + 16 + 16 bytes per point,
+// each on tiles that one CTA owns.  With the factorisation of propagate.cuh and the point-2 row
+// index split as c = r + 4 m (r < 4, m < 64), k_c = k_l + 64 k_h:
+//   e^{-2 pi i c k_c / 256} = e^{-2 pi i r k_h / 4} e^{-2 pi i r k_l / 256} e^{-2 pi i m k_l / 64},
+// so the point-2 transform is a DFT-64 over m and a DFT-256 over d for each r (pass 1), then a
+// twiddle e^{-2 pi i r k_l / 256} and a DFT-4 over r (pass 2).
+//   pass 1, tile (a, b, r): the source rows c = r + 4 m of slice (a, b) are generated in registers
+//     (W1(c, d) = conj F(a, b) F(c, d) x source), transformed over (m, d) as a 64 x 256 2D DFT in
+//     registers through one shared buffer, and stored to Y1[a][b][r][k_l][d'] (work).
+//   pass 2, tile (a, k_l, 8 consecutive d'): the 256 x 4 x 8 block Y1[a][.][.][k_l][d'] arrives by
+//     one TMA tensor load; twiddle e^{-2 pi i r k_l / 256}, DFT-4 over r (-> k_h), DFT-256 over b
+//     (sign +1); stored in W's own layout as Y2 at W[a][b'][k_c][d'].
+//   pass 3, tile (b', c', 32 consecutive d'): the 256 x 32 block W[.][b'][c'][d'] arrives by one
+//     TMA tensor load; DFT-256 over a (sign +1), output propagators, scale and S; stored back to
+//     the same addresses (the tile reads and writes one set of addresses).
+// Passes 2 and 3 run two CTAs per SM, so that one CTA's tile load overlaps the other's DFT.  None
+// of the passes needs a Hermitian source.
+#pragma once
+#include <cuda.h>
+#include <cstdint>
+
+#include "propagate.cuh"
+#include "r128.cuh"
+#include "tc16.cuh"
+
+namespace pw {
+namespace t256 {
+
+constexpr int N = 256;
+constexpr int NT1 = 512;  // pass 1: 32 points per thread of a 64 x 256 tile
+constexpr int NT2 = 256;  // passes 2 and 3: 32 points per thread of an 8192-point tile
+
+// ---- TMA tensor loads into shared memory, completing on an mbarrier ----
+__device__ __forceinline__ void mbar_expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void* smem, const void* tmap, uint64_t* mbar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], "
+      "[%2];" ::"r"(smem_u32(smem)),
+      "l"(tmap), "r"(smem_u32(mbar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* smem, const void* tmap, uint64_t* mbar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(smem_u32(smem)),
+      "l"(tmap), "r"(smem_u32(mbar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int m) {
+  float2 w = tw[m & (N - 1)];
+  if (SIGN > 0) w.y = -w.y;
+  return w;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass 1.  Tile (a, b, r): T(m, d) = W1(a, b, r + 4 m, d), m < 64, d < 256, 512 threads (warp w,
+// lane l).  The 2D DFT (sign -1) over (m, d) runs as three 2D Stockham stages (p = m, q = d):
+//   stage 1: radices (4, 8), butterfly (jp = w, jq = l), inputs (w + 16 rp, l + 32 rq), the
+//            thread's own generated points; outputs (4 jp + rp, 8 jq + rq);
+//   stage 2: radices (4, 8), NS = (4, 8), butterfly (w, l), inputs (w + 16 rp, l + 32 rq),
+//            twiddles w16^(rp (jp mod 4)) w64^(rq (jq mod 8)); outputs (16 (jp / 4) + jp mod 4 +
+//            4 rp, 64 (jq / 8) + jq mod 8 + 8 rq);
+//   stage 3: radices (4, 4), NS = (16, 64), butterflies (w, l + 32 h), h < 2, inputs
+//            (jp + 16 rp, jq + 64 rq), twiddles w64^(rp jp) w256^(rq jq); outputs in natural order
+//            (k_l, d') at the input positions;
+// (w_L = e^{-2 pi i / L}).  The two exchanges go through one 128 KB buffer whose column index is
+// XOR-swizzled per exchange so that every access of a warp touches each 8-byte bank pair twice:
+//   exchange 1: q ^ ((q >> 4) & 7);  exchange 2: q ^ (((q >> 6) & 3) << 3).
+// The outputs go to Y1[a][b][r][k_l][d'] straight from registers (each warp store is 256 contiguous
+// bytes); the twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue slots to spare.
+__device__ __forceinline__ int xs1(int q) { return q ^ ((q >> 4) & 7); }
+__device__ __forceinline__ int xs2(int q) { return q ^ (((q >> 6) & 3) << 3); }
+
+constexpr size_t pass1_smem() { return (size_t)64 * N * sizeof(float2) + N * sizeof(float2); }
+
+template <int SRC>
+__global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __restrict__ Y1) {
+  constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
+  extern __shared__ __align__(1024) float2 smem[];
+  float2* buf = smem;  // 64 x 256
+  float2* tw = buf + 64 * N;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int i = t; i < N; i += NT1) tw[i] = p.tw[i];
+  const float2* __restrict__ F = p.F;
+  const float* __restrict__ G = p.G;
+  for (int tile = blockIdx.x; tile < N * N * 4; tile += gridDim.x) {
+    const int ab = tile >> 2, r = tile & 3;
+    const int a = ab / N, b = ab - a * N;
+    float2 s_ab = cconj(__ldg(F + ab));
+    if (SRC == SRC_GSM || SRC == SRC_ADJ) s_ab = cscale(s_ab, p.A);
+    if (DIAG) s_ab = cscale(s_ab, p.A * __ldg(p.diag + ab));
+    const float2* W0 = ARRAY ? p.W0 + (size_t)ab * N * N : nullptr;
+    AdjSlice adj{};
+    if (SRC == SRC_ADJ) adj = adj_slice(p, ab, N);
+    // stage 1 inputs: m = w + 16 rp (c = r + 4 m), d = l + 32 rq
+    float gb[8];
+    if (SRC == SRC_GSM) {
+#pragma unroll
+      for (int rq = 0; rq < 8; ++rq) gb[rq] = __ldg(G + b * N + lane + 32 * rq);
+    }
+    float2 v[4][8];
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp) {
+      const int c = r + 4 * (w + 16 * rp);
+      const float ga = SRC == SRC_GSM ? __ldg(G + a * N + c) : 1.f;
+#pragma unroll
+      for (int rq = 0; rq < 8; ++rq) {
+        const int d = lane + 32 * rq;
+        float2 x = cmul(s_ab, __ldg(F + c * N + d));
+        if (SRC == SRC_GSM) x = cscale(x, ga * gb[rq]);
+        if (ARRAY) x = cmul(x, __ldg(W0 + c * N + d));
+        if (DIAG) x = (c == a && d == b) ? x : make_float2(0.f, 0.f);
+        if (SRC == SRC_ADJ) x = cmul(x, adj.at(p.cross, c * N + d));
+        v[rp][rq] = x;
+      }
+    }
+    r128::dft2d<4, 8, -1>(v);
+    __syncthreads();  // tw (first tile); every read of buf of the previous tile is done
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 8; ++rq) buf[(4 * w + rp) * N + xs1(8 * lane + rq)] = v[rp][rq];
+    __syncthreads();
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 8; ++rq) v[rp][rq] = buf[(w + 16 * rp) * N + xs1(lane + 32 * rq)];
+    r128::twiddle2d<4, 8, -1>(v, tw, 16 * (w & 3), 4 * (lane & 7));
+    r128::dft2d<4, 8, -1>(v);
+    __syncthreads();
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+      for (int rq = 0; rq < 8; ++rq)
+        buf[(16 * (w >> 2) + (w & 3) + 4 * rp) * N + xs2(64 * (lane >> 3) + (lane & 7) + 8 * rq)] = v[rp][rq];
+    __syncthreads();
+    float2* Yt = Y1 + (size_t)tile * 64 * N;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jq = lane + 32 * h;
+      float2 u[4][4];
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+        for (int rq = 0; rq < 4; ++rq) u[rp][rq] = buf[(w + 16 * rp) * N + xs2(jq + 64 * rq)];
+      r128::twiddle2d<4, 4, -1>(u, tw, 4 * w, jq);
+      r128::dft2d<4, 4, -1>(u);
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+        for (int rq = 0; rq < 4; ++rq) Yt[(w + 16 * rp) * N + jq + 64 * rq] = u[rp][rq];
+    }
+  }
+}
+
+// Bounded wait on the tile load of a pass-2/3 CTA; every thread learns the outcome.  A wait that
+// gives up sets *err; the caller leaves its loop (after which no load of its own is in flight
+// that it has not waited for, up to the bound).
+__device__ __forceinline__ bool tile_arrived(uint64_t* mbar, uint32_t parity, int* err) {
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    ok = tc16::mbar_wait(mbar, parity) ? 1 : 0;
+    if (!ok) atomicExch(err, 1);
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass 2.  Tile (a, k_l, db): X[b][r][j] = Y1[a][b][r][k_l][8 db + j] (b < 256, r < 4, j < 8),
+// 64 KB by one TMA load (tensor map: Y1 as floats {512, 64, 4, 256, 256}, box {16, 1, 4, 256, 1}).
+//   phase 1: twiddle e^{-2 pi i r k_l / 256} and DFT-4 over r (sign -1) for each (b, j), in place
+//            (r -> k_h);
+//   phase 2: DFT-256 over b (sign +1), first radix-16 stage: line L = (k_h, j) = lane, butterflies
+//            n1 = w and w + 8, inputs b = n1 + 16 n2, twiddle w256^(n1 k2), in place;
+//   phase 3: second stage: butterflies k2 = w, w + 8, inputs n1 + 16 k2, outputs b' = k2 + 16 k1.
+// Outputs go to W[a][b'][k_l + 64 k_h][8 db + j] (runs of 64 bytes).  The next tile's load is
+// issued once every thread has read the buffer.
+constexpr size_t pass2_smem() { return (size_t)N * 4 * 8 * sizeof(float2) + N * sizeof(float2) + 64; }
+
+__global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ CUtensorMap ymap, const float2* tw_g,
+                                                     float2* __restrict__ W, int* err) {
+  extern __shared__ __align__(1024) float2 smem[];
+  float2* X = smem;  // [256][4][8]
+  float2* tw = X + N * 32;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + N);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int i = t; i < N; i += NT2) tw[i] = tw_g[i];
+  constexpr int NTILES = N * 64 * 32;
+  auto issue = [&](int tile) {
+    const int db = tile & 31, kl = (tile >> 5) & 63, a = tile >> 11;
+    fence_proxy_async_smem();
+    mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
+    tma_load_5d(X, &ymap, mbar, 16 * db, kl, 0, 0, a);
+  };
+  bool pending = false;  // thread 0: a load was issued and not yet seen complete
+  if (t == 0) {
+    tc16::mbar_init(mbar);
+    if ((int)blockIdx.x < NTILES) {
+      issue(blockIdx.x);
+      pending = true;
+    }
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (int tile = blockIdx.x; tile < NTILES; tile += gridDim.x, parity ^= 1u) {
+    const int db = tile & 31, kl = (tile >> 5) & 63, a = tile >> 11;
+    if (!tile_arrived(mbar, parity, err)) break;
+    pending = false;
+    // phase 1: (b, j) pairs u = t + 256 i, b = u >> 3, j = u & 7: twiddle e^{-2 pi i r k_l / 256}, DFT-4
+    const float2 tr1 = twid<-1>(tw, kl), tr2 = twid<-1>(tw, 2 * kl), tr3 = twid<-1>(tw, 3 * kl);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int u = t + NT2 * i, bb = u >> 3, j = u & 7;
+      float2 x[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x[r] = X[bb * 32 + r * 8 + j];
+      x[1] = cmul(x[1], tr1);
+      x[2] = cmul(x[2], tr2);
+      x[3] = cmul(x[3], tr3);
+      Dft<4, -1>::run(x);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) X[bb * 32 + r * 8 + j] = x[r];
+    }
+    __syncthreads();
+    // phase 2: lines L = lane, n1 = w, w + 8
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int n1 = w + 8 * e;
+      float2 x[16];
+#pragma unroll
+      for (int n2 = 0; n2 < 16; ++n2) x[n2] = X[(n1 + 16 * n2) * 32 + lane];
+      Dft<16, +1>::run(x);
+#pragma unroll
+      for (int k2 = 1; k2 < 16; ++k2) x[k2] = cmul(x[k2], twid<+1>(tw, n1 * k2));
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) X[(n1 + 16 * k2) * 32 + lane] = x[k2];
+    }
+    __syncthreads();
+    float2 y[2][16];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k2 = w + 8 * e;
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) y[e][n1] = X[(n1 + 16 * k2) * 32 + lane];
+      Dft<16, +1>::run(y[e]);
+    }
+    __syncthreads();  // every thread has read X: the next tile may land there
+    if (t == 0 && tile + (int)gridDim.x < NTILES) {
+      issue(tile + gridDim.x);
+      pending = true;
+    }
+    const int kc = kl + 64 * (lane >> 3), dq = 8 * db + (lane & 7);
+    float2* Wa = W + (size_t)a * N * N * N + (size_t)kc * N + dq;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k2 = w + 8 * e;
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) Wa[(size_t)(k2 + 16 * k1) * N * N] = y[e][k1];
+    }
+  }
+  if (t == 0 && pending) tc16::mbar_wait(mbar, parity);  // a load left in flight by a failed wait
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass 3.  Tile (b', c', db): X[a][j] = W[a][b'][c'][32 db + j] (a < 256, j < 32), 64 KB by one TMA
+// load (tensor map: W as floats {512, 256, 256, 256}, box {64, 1, 1, 256}).  DFT-256 over a (sign
+// +1) as two radix-16 stages (line j = lane; butterflies 2 w, 2 w + 1), then the epilogue
+// W_B = s conj(E(a') E(b')) E(c') E(d') X and S on the diagonal, stored to the addresses the tile
+// was loaded from.
+constexpr size_t pass3_smem() { return (size_t)N * 32 * sizeof(float2) + 2 * N * sizeof(float2) + 64; }
+
+__global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ CUtensorMap wmap, PassBArgs p,
+                                                     int* err) {
+  extern __shared__ __align__(1024) float2 smem[];
+  float2* X = smem;  // [256][32]
+  float2* tw = X + N * 32;
+  float2* eo = tw + N;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(eo + N);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int i = t; i < N; i += NT2) {
+    tw[i] = p.tw[i];
+    eo[i] = p.Eout[i];
+  }
+  constexpr int NTILES = N * N * 8;
+  auto issue = [&](int tile) {
+    const int db = tile & 7, cq = (tile >> 3) & 255, bq = tile >> 11;
+    fence_proxy_async_smem();
+    mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
+    tma_load_4d(X, &wmap, mbar, 64 * db, cq, bq, 0);
+  };
+  bool pending = false;  // thread 0: a load was issued and not yet seen complete
+  if (t == 0) {
+    tc16::mbar_init(mbar);
+    if ((int)blockIdx.x < NTILES) {
+      issue(blockIdx.x);
+      pending = true;
+    }
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (int tile = blockIdx.x; tile < NTILES; tile += gridDim.x, parity ^= 1u) {
+    const int db = tile & 7, cq = (tile >> 3) & 255, bq = tile >> 11;
+    if (!tile_arrived(mbar, parity, err)) break;
+    pending = false;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int n1 = 2 * w + e;
+      float2 x[16];
+#pragma unroll
+      for (int n2 = 0; n2 < 16; ++n2) x[n2] = X[(n1 + 16 * n2) * 32 + lane];
+      Dft<16, +1>::run(x);
+#pragma unroll
+      for (int k2 = 1; k2 < 16; ++k2) x[k2] = cmul(x[k2], twid<+1>(tw, n1 * k2));
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) X[(n1 + 16 * k2) * 32 + lane] = x[k2];
+    }
+    __syncthreads();
+    float2 y[2][16];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k2 = 2 * w + e;
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) y[e][n1] = X[(n1 + 16 * k2) * 32 + lane];
+      Dft<16, +1>::run(y[e]);
+    }
+    __syncthreads();  // every thread has read X: the next tile may land there
+    if (t == 0 && tile + (int)gridDim.x < NTILES) {
+      issue(tile + gridDim.x);
+      pending = true;
+    }
+    const int dq = 32 * db + lane;
+    const float2 e_bcd = cscale(cmul(cconj(eo[bq]), cmul(eo[cq], eo[dq])), p.scale);
+    float2* Wt = p.W + ((size_t)bq * N + cq) * N + dq;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k2 = 2 * w + e;
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) {
+        const int aq = k2 + 16 * k1;
+        const float2 v = cmul(cmul(cconj(eo[aq]), e_bcd), y[e][k1]);
+        Wt[(size_t)aq * N * N * N] = v;
+        if (aq == cq && dq == bq) p.S[cq * N + bq] = v.x;
+      }
+    }
+  }
+  if (t == 0 && pending) tc16::mbar_wait(mbar, parity);  // a load left in flight by a failed wait
+  __syncthreads();
+}
+
+}  // namespace t256
+}  // namespace pw

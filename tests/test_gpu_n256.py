@@ -219,3 +219,71 @@ def test_dft_mode_arguments():
         pw.pw_csd_set_dft_mode(h, pw.PW_DFT_TC_BF16X3)
     assert pw.pw_csd_get_dft_mode(h) == pw.PW_DFT_AUTO
     pw.pw_csd_destroy(h)
+
+
+def test_n256_adjoint_dot_product_identity():
+    """The adjoint at N = 256 (three-pass engine, the general non-Hermitian adjoint of a loss on S and
+    mu): for the linear loss L(W_B) = Re <2 Y, W_B> with Y the adjoint source of gradients (gS, gmu)
+    (reading R22), dL/dW0 = 2 P^H(Y), so Re <dL/dW0, W0> must equal Re <2 Y, P(W0)> -- the left side
+    from the gradient the call writes over the whole N^4 array, the right side from S and the P1 row
+    of the forward propagation (FP64 sums on both sides)."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    cfg = WL.PHASE_SCREEN_N256
+    N, dxi, lam, z = cfg["N"], cfg["dxi"], cfg["lam"], cfg["z"]
+    P1 = tuple(cfg["P1"])
+    mask = WL.to_c64(WL.phase_screen(N, seed=WL.SEED, corr_px=cfg["corr_px"]))
+    c = pw.CSD(N, dxi, lam)
+    mt = torch.from_numpy(mask).cuda()
+    c.source_gsm(cfg["sigma_S"], cfg["sigma_mu"], cfg["A"])
+    c.source_mask(mt)
+    c.propagate_fresnel(z)
+    S = c.spectral_density()
+    mu = c.degree_of_coherence(*P1)
+    row = c.W[P1[0], P1[1]].clone()
+    torch.cuda.synchronize()
+    # positive dL/dS (no cancellation in the reference sum), and a random dL/dmu on S >= 1e-4 max S
+    # scaled so that the mu terms are about 1 % of the total: the mu part of a linear loss cancels
+    # between the P1 row and the diagonal (mu is scale-free), so a wrong row adjoint shows at that level
+    Sh0 = S.cpu().numpy().astype(np.float64)
+    gS_h = 0.5 + 0.5 * WL.uniform01(71, N * N).reshape(N, N)
+    u = WL.uniform01(72, 2 * N * N).reshape(2, N, N) - 0.5
+    region = Sh0 >= 1e-4 * Sh0.max()
+    scale = 0.01 * np.sum(gS_h * Sh0) / max(float(np.sum(np.abs(mu.cpu().numpy())[region])), 1e-30)
+    gS = torch.tensor(gS_h, dtype=torch.float32, device="cuda")
+    gmu = torch.tensor(np.where(region, scale * (u[0] + 1j * u[1]), 0.0), dtype=torch.complex64, device="cuda")
+    adj = pw.pw_adjoint()
+    adj.dev_dS, adj.dev_dmu, adj.iP, adj.jP = gS.data_ptr(), gmu.data_ptr(), P1[0], P1[1]
+    adj.dev_S, adj.dev_mu, adj.grad_W0 = S.data_ptr(), mu.data_ptr(), 1
+    pw.pw_propagate_fresnel_adjoint(c.h, z, adj)
+    pw.pw_csd_check(c.h)
+    # left: Re <g, W0> with W0 = A conj(m(x1)) g(a,c) g(b,d) m(x2) generated slice block by slice block
+    x, _ = O.axis_coords(N, dxi)
+    gax = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * cfg["sigma_S"] ** 2)
+                 - (x[:, None] - x[None, :]) ** 2 / (2 * cfg["sigma_mu"] ** 2))
+    gt = torch.tensor(gax, dtype=torch.float64, device="cuda")
+    m64 = torch.tensor(mask.astype(np.complex128), device="cuda")
+    left = 0.0
+    for a in range(N):
+        # W0[a, b, c, d] = A conj(m[a, b]) g[a, c] g[b, d] m[c, d]
+        blk = (cfg["A"] * torch.conj(m64[a])[:, None, None] * gt[a][None, :, None] * gt[:, None, :]) * m64[None]
+        left += float(torch.sum(torch.conj(c.W[a].cdouble()) * blk).real)
+    c.close()
+    # right: Re <2 Y, W_B> from S and the P1 row, Y built from the same FP32 S and mu (R22)
+    Sh = S.cpu().numpy().astype(np.float64)
+    muh = mu.cpu().numpy().astype(np.complex128)
+    rowh = row.cpu().numpy().astype(np.complex128)
+    gSh = gS.cpu().numpy().astype(np.float64)
+    gmuh = gmu.cpu().numpy().astype(np.complex128)
+    sp = Sh[P1]
+    ok = sp * Sh > 0
+    D = np.sqrt(np.where(ok, sp * Sh, 1.0))
+    r = np.where(ok, np.real(np.conj(gmuh) * muh), 0.0)
+    dS = gSh - np.where(ok & (Sh > 0), r / (2 * np.where(Sh > 0, Sh, 1.0)), 0.0)
+    dS[P1] -= r.sum() / (2 * sp)
+    gw = np.where(ok, gmuh / D, 0.0)
+    right = float(np.sum(dS * Sh) + np.real(np.sum(np.conj(gw) * rowh)))
+    from gpu_cases import record
+    e = abs(left - right) / abs(right)
+    record("n256_adjoint_dot", left=left, right=right, rel=e)
+    assert e < 1e-5, (left, right, e)
