@@ -62,6 +62,8 @@ def parse_args():
                    help="default: the N = 256 phase-screen workload (with the N = 128 one inside its line)")
     p.add_argument("--headline-only", action="store_true",
                    help="with the default workload: skip the N = 128 measurement reported inside the line")
+    p.add_argument("--skip-cpu", action="store_true",
+                   help="leave out the two CPU baselines (for profiler runs of the GPU kernels)")
     p.add_argument("--dft", choices=["auto", "fp32", "tc_bf16x3"], default="auto",
                    help="arithmetic of the DFT work with a tensor-core form (the N = 256 first stage, the dense "
                         "contractions of padded workloads): auto (the library's per-path default), FP32 on the "
@@ -538,7 +540,7 @@ def run_ours(args):
     if second is not None:
         line["n128"] = {k: second[k] for k in ("value", "ms_per_step", "config", "roofline", "e2e", "clocks")}
         line["n128"]["unit"] = UNIT
-    if world == 1:
+    if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_plain_fp32"] = cpu_plain_fp32()
     print(json.dumps(line), flush=True)
