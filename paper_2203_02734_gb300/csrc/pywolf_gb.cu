@@ -102,7 +102,7 @@ struct pw_csd {
   const pw::GradEpi* adj_grad;  // non-null: reduce the GSM parameter gradients in pass B (W_GRAD)
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
   CUtensorMap ymap;  // N = 256: the second pass's tiles of Y1 (work buffer)
-  CUtensorMap wmap;  // N = 256: the third pass's tiles of W
+  CUtensorMap y3map;  // N = 256: the third pass's tiles of the work buffer
   int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
   void* qbuf;        // split DFT matrices of the tensor-core dense path (allocated on first use)
@@ -414,32 +414,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// N = 256 (three-pass engine): Y1[a][b][r][k_l][d'] in the work buffer as floats {2N, 64, 4, N, N}
-// with the second pass's box {16, 1, 4, N, 1} (8 d' x 4 r x all b), and W[a][b'][c'][d'] as floats
-// {2N, N, N, N} with the third pass's box {64, 1, 1, N} (32 d' x all a).
+// N = 256 (three-pass engine): Y[a][b][k_l][d' / 8][r][d' mod 8] in the work buffer as floats
+// {64, 32, 64, N, N} (the innermost 64 floats are one 256-byte run of 4 r x 8 d'), with the second
+// pass's box {64, 1, 1, N, 1} (one run for every b) and the third pass's box {16, 4, 1, 1, N} (the
+// 64-byte pieces of one k_h in four consecutive runs, for every a).
 pw_status make_t256_maps(pw_csd* h) {
   auto enc = encode_tiled();
   if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-  constexpr cuuint64_t N = 256, row = 2 * N * sizeof(float);
+  constexpr cuuint64_t N = 256, run = 64 * sizeof(float);
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  {
-    cuuint64_t dims[5] = {2 * N, 64, 4, N, N};
-    cuuint64_t strides[4] = {row, row * 64, row * 64 * 4, row * 64 * 4 * N};
-    cuuint32_t box[5] = {16, 1, 4, (cuuint32_t)N, 1};
-    CUresult r = enc(&h->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->work, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (second-pass tiles) failed (CUresult %d)", (int)r);
-  }
-  {
-    cuuint64_t dims[4] = {2 * N, N, N, N};
-    cuuint64_t strides[3] = {row, row * N, row * N * N};
-    cuuint32_t box[4] = {64, 1, 1, (cuuint32_t)N};
-    CUresult r = enc(&h->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->W, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (third-pass tiles) failed (CUresult %d)", (int)r);
-  }
+  const cuuint64_t dims[5] = {64, 32, 64, N, N};
+  const cuuint64_t strides[4] = {run, run * 32, run * 32 * 64, run * 32 * 64 * N};
+  const cuuint32_t box2[5] = {64, 1, 1, (cuuint32_t)N, 1}, box3[5] = {16, 4, 1, 1, (cuuint32_t)N};
+  CUresult r = enc(&h->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->work, dims, strides, box2, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (second-pass tiles) failed (CUresult %d)", (int)r);
+  r = enc(&h->y3map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->work, dims, strides, box3, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (third-pass tiles) failed (CUresult %d)", (int)r);
   return PW_OK;
 }
 
@@ -606,9 +600,10 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
 }
 
 // N = 256, three streaming passes (t256.cuh): the source with the point-2 DFT over (m, d) into the
-// work buffer, the radix-4 over r and the DFT over b into W, the DFT over a with the output factors
-// and S in place in W.  Any source (Hermitian or not).  Events: the first pass, then the second and
-// third apart.
+// work buffer, the radix-4 over r and the DFT over b in place there, the DFT over a with the output
+// factors and S from the work buffer into W.  Any source (Hermitian or not; an uploaded W0 may be W
+// itself, since the first pass writes only the work buffer).  Events: the first pass, then the
+// second and third apart.
 pw_status propagate_t256(pw_csd* h, double z, bool herm) {
   namespace T = pw::t256;
   const int src = h->kind == SRC_GSM ? pw::SRC_GSM
@@ -672,10 +667,10 @@ pw_status propagate_t256(pw_csd* h, double z, bool herm) {
   }
   if (e != cudaSuccess) return cuda_fail(e, "first-pass launch (N = 256)");
   if (ev && (e = cudaEventRecord(ev[1], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
-  T::pass2_kernel<<<g2, T::NT2, T::pass2_smem(), h->stream>>>(h->ymap, h->tw, reinterpret_cast<float2*>(h->W), h->err);
+  T::pass2_kernel<<<g2, T::NT2, T::pass2_smem(), h->stream>>>(h->ymap, h->tw, reinterpret_cast<float2*>(h->work), h->err);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "second-pass launch (N = 256)");
   if (ev && (e = cudaEventRecord(ev[3], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
-  T::pass3_kernel<<<g3, T::NT2, T::pass3_smem(), h->stream>>>(h->wmap, b, h->err);
+  T::pass3_kernel<<<g3, T::NT2, T::pass3_smem(), h->stream>>>(h->y3map, b, h->err);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "third-pass launch (N = 256)");
   if (ev && (e = cudaEventRecord(ev[2], h->stream)) != cudaSuccess) return cuda_fail(e, "event record");
   h->d = lz / (h->N * h->d);

@@ -7,16 +7,21 @@
 // index split as c = r + 4 m (r < 4, m < 64), k_c = k_l + 64 k_h:
 //   e^{-2 pi i c k_c / 256} = e^{-2 pi i r k_h / 4} e^{-2 pi i r k_l / 256} e^{-2 pi i m k_l / 64},
 // so the point-2 transform is a DFT-64 over m and a DFT-256 over d for each r (pass 1), then a
-// twiddle e^{-2 pi i r k_l / 256} and a DFT-4 over r (pass 2).
+// twiddle e^{-2 pi i r k_l / 256} and a DFT-4 over r (pass 2).  With d' = 8 g + j (j < 8) the
+// intermediate array lives in the work buffer as
+//   Y[a][b][k_l][g][r][j]  (after pass 1)  and  Y[a][b'][k_l][g][k_h][j]  (after pass 2),
+// so that the 4 x 8 values one pass-2 line group needs are one 256-byte run.
 //   pass 1, tile (a, b, r): the source rows c = r + 4 m of slice (a, b) are generated in registers
 //     (W1(c, d) = conj F(a, b) F(c, d) x source), transformed over (m, d) as a 64 x 256 2D DFT in
-//     registers through one shared buffer, and stored to Y1[a][b][r][k_l][d'] (work).
-//   pass 2, tile (a, k_l, 8 consecutive d'): the 256 x 4 x 8 block Y1[a][.][.][k_l][d'] arrives by
-//     one TMA tensor load; twiddle e^{-2 pi i r k_l / 256}, DFT-4 over r (-> k_h), DFT-256 over b
-//     (sign +1); stored in W's own layout as Y2 at W[a][b'][k_c][d'].
-//   pass 3, tile (b', c', 32 consecutive d'): the 256 x 32 block W[.][b'][c'][d'] arrives by one
-//     TMA tensor load; DFT-256 over a (sign +1), output propagators, scale and S; stored back to
-//     the same addresses (the tile reads and writes one set of addresses).
+//     registers through one shared buffer, and stored to Y (64-byte pieces of the 256-byte runs;
+//     the four r tiles of a slice run side by side and fill each run together).
+//   pass 2, tile (a, k_l, g): the 256 runs Y[a][.][k_l][g] (all b, r, j) arrive by one TMA tensor
+//     load; twiddle e^{-2 pi i r k_l / 256}, DFT-4 over r (-> k_h), DFT-256 over b (sign +1);
+//     stored back to the same runs (the tile reads and writes one set of addresses).
+//   pass 3, tile (b', c' = k_l + 64 k_h, 32 consecutive d'): the 256 x 32 block arrives by one TMA
+//     tensor load (four 64-byte pieces per a); DFT-256 over a (sign +1), output propagators,
+//     scale and S; stored to W[a][b'][c'][d'] in 256-byte runs.  The four k_h tiles of a run group
+//     are consecutive, so the pieces of each 256-byte run are read at about the same time.
 // Passes 2 and 3 run two CTAs per SM, so that one CTA's tile load overlaps the other's DFT.  None
 // of the passes needs a Hermitian source.
 #pragma once
@@ -46,15 +51,6 @@ __device__ __forceinline__ void tma_load_5d(void* smem, const void* tmap, uint64
       "l"(tmap), "r"(smem_u32(mbar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
       : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(void* smem, const void* tmap, uint64_t* mbar, int c0, int c1, int c2,
-                                            int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-      "[%2];" ::"r"(smem_u32(smem)),
-      "l"(tmap), "r"(smem_u32(mbar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
 template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int m) {
   float2 w = tw[m & (N - 1)];
   if (SIGN > 0) w.y = -w.y;
@@ -75,8 +71,9 @@ template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int
 // (w_L = e^{-2 pi i / L}).  The two exchanges go through one 128 KB buffer whose column index is
 // XOR-swizzled per exchange so that every access of a warp touches each 8-byte bank pair twice:
 //   exchange 1: q ^ ((q >> 4) & 7);  exchange 2: q ^ (((q >> 6) & 3) << 3).
-// The outputs go to Y1[a][b][r][k_l][d'] straight from registers (each warp store is 256 contiguous
-// bytes); the twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue slots to spare.
+// The outputs go to Y[a][b][k_l][d' / 8][r][d' mod 8] straight from registers (each warp store is
+// four 64-byte pieces); the twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue
+// slots to spare.
 __device__ __forceinline__ int xs1(int q) { return q ^ ((q >> 4) & 7); }
 __device__ __forceinline__ int xs2(int q) { return q ^ (((q >> 6) & 3) << 3); }
 
@@ -143,7 +140,7 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __re
       for (int rq = 0; rq < 8; ++rq)
         buf[(16 * (w >> 2) + (w & 3) + 4 * rp) * N + xs2(64 * (lane >> 3) + (lane & 7) + 8 * rq)] = v[rp][rq];
     __syncthreads();
-    float2* Yt = Y1 + (size_t)tile * 64 * N;
+    float2* Ys = Y1 + (size_t)ab * N * N + 8 * r;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int jq = lane + 32 * h;
@@ -157,7 +154,7 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __re
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-        for (int rq = 0; rq < 4; ++rq) Yt[(w + 16 * rp) * N + jq + 64 * rq] = u[rp][rq];
+        for (int rq = 0; rq < 4; ++rq) Ys[(w + 16 * rp) * 1024 + (jq >> 3) * 32 + (jq & 7) + 256 * rq] = u[rp][rq];
     }
   }
 }
@@ -175,19 +172,20 @@ __device__ __forceinline__ bool tile_arrived(uint64_t* mbar, uint32_t parity, in
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pass 2.  Tile (a, k_l, db): X[b][r][j] = Y1[a][b][r][k_l][8 db + j] (b < 256, r < 4, j < 8),
-// 64 KB by one TMA load (tensor map: Y1 as floats {512, 64, 4, 256, 256}, box {16, 1, 4, 256, 1}).
+// Pass 2.  Tile (a, k_l, g): X[b][r][j] = Y[a][b][k_l][g][r][j] (b < 256, r < 4, j < 8), 64 KB by
+// one TMA load (tensor map: Y as floats {64, 32, 64, 256, 256}, box {64, 1, 1, 256, 1}).
 //   phase 1: twiddle e^{-2 pi i r k_l / 256} and DFT-4 over r (sign -1) for each (b, j), in place
 //            (r -> k_h);
 //   phase 2: DFT-256 over b (sign +1), first radix-16 stage: line L = (k_h, j) = lane, butterflies
 //            n1 = w and w + 8, inputs b = n1 + 16 n2, twiddle w256^(n1 k2), in place;
 //   phase 3: second stage: butterflies k2 = w, w + 8, inputs n1 + 16 k2, outputs b' = k2 + 16 k1.
-// Outputs go to W[a][b'][k_l + 64 k_h][8 db + j] (runs of 64 bytes).  The next tile's load is
-// issued once every thread has read the buffer.
+// Outputs go back to the runs they came from, Y[a][b'][k_l][g][k_h][j] (line L = 8 k_h + j = lane:
+// one 256-byte run per warp store).  The next tile's load is issued once every thread has read the
+// buffer.
 constexpr size_t pass2_smem() { return (size_t)N * 4 * 8 * sizeof(float2) + N * sizeof(float2) + 64; }
 
 __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ CUtensorMap ymap, const float2* tw_g,
-                                                     float2* __restrict__ W, int* err) {
+                                                     float2* __restrict__ Y, int* err) {
   extern __shared__ __align__(1024) float2 smem[];
   float2* X = smem;  // [256][4][8]
   float2* tw = X + N * 32;
@@ -199,7 +197,7 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
     const int db = tile & 31, kl = (tile >> 5) & 63, a = tile >> 11;
     fence_proxy_async_smem();
     mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
-    tma_load_5d(X, &ymap, mbar, 16 * db, kl, 0, 0, a);
+    tma_load_5d(X, &ymap, mbar, 0, db, kl, 0, a);
   };
   bool pending = false;  // thread 0: a load was issued and not yet seen complete
   if (t == 0) {
@@ -258,13 +256,12 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
       issue(tile + gridDim.x);
       pending = true;
     }
-    const int kc = kl + 64 * (lane >> 3), dq = 8 * db + (lane & 7);
-    float2* Wa = W + (size_t)a * N * N * N + (size_t)kc * N + dq;
+    float2* Ya = Y + (size_t)a * N * N * N + kl * 1024 + db * 32 + lane;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int k2 = w + 8 * e;
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) Wa[(size_t)(k2 + 16 * k1) * N * N] = y[e][k1];
+      for (int k1 = 0; k1 < 16; ++k1) Ya[(size_t)(k2 + 16 * k1) * N * N] = y[e][k1];
     }
   }
   if (t == 0 && pending) tc16::mbar_wait(mbar, parity);  // a load left in flight by a failed wait
@@ -272,14 +269,14 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pass 3.  Tile (b', c', db): X[a][j] = W[a][b'][c'][32 db + j] (a < 256, j < 32), 64 KB by one TMA
-// load (tensor map: W as floats {512, 256, 256, 256}, box {64, 1, 1, 256}).  DFT-256 over a (sign
+// Pass 3.  Tile (k_h, q, k_l, b'), k_h fastest: c' = k_l + 64 k_h, d' = 32 q + j,
+// X[a][j] = Y[a][b'][k_l][4 q + j / 8][k_h][j mod 8] (a < 256, j < 32), 64 KB by one TMA load
+// (tensor map: Y as floats {64, 32, 64, 256, 256}, box {16, 4, 1, 1, 256}).  DFT-256 over a (sign
 // +1) as two radix-16 stages (line j = lane; butterflies 2 w, 2 w + 1), then the epilogue
-// W_B = s conj(E(a') E(b')) E(c') E(d') X and S on the diagonal, stored to the addresses the tile
-// was loaded from.
+// W_B = s conj(E(a') E(b')) E(c') E(d') X and S on the diagonal, stored to W[a'][b'][c'][d'].
 constexpr size_t pass3_smem() { return (size_t)N * 32 * sizeof(float2) + 2 * N * sizeof(float2) + 64; }
 
-__global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ CUtensorMap wmap, PassBArgs p,
+__global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ CUtensorMap y3map, PassBArgs p,
                                                      int* err) {
   extern __shared__ __align__(1024) float2 smem[];
   float2* X = smem;  // [256][32]
@@ -293,10 +290,10 @@ __global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ C
   }
   constexpr int NTILES = N * N * 8;
   auto issue = [&](int tile) {
-    const int db = tile & 7, cq = (tile >> 3) & 255, bq = tile >> 11;
+    const int kh = tile & 3, q = (tile >> 2) & 7, kl = (tile >> 5) & 63, bq = tile >> 11;
     fence_proxy_async_smem();
     mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
-    tma_load_4d(X, &wmap, mbar, 64 * db, cq, bq, 0);
+    tma_load_5d(X, &y3map, mbar, 16 * kh, 4 * q, kl, bq, 0);
   };
   bool pending = false;  // thread 0: a load was issued and not yet seen complete
   if (t == 0) {
@@ -309,7 +306,7 @@ __global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ C
   __syncthreads();
   uint32_t parity = 0;
   for (int tile = blockIdx.x; tile < NTILES; tile += gridDim.x, parity ^= 1u) {
-    const int db = tile & 7, cq = (tile >> 3) & 255, bq = tile >> 11;
+    const int q = (tile >> 2) & 7, bq = tile >> 11, cq = ((tile >> 5) & 63) + 64 * (tile & 3);
     if (!tile_arrived(mbar, parity, err)) break;
     pending = false;
 #pragma unroll
@@ -338,7 +335,7 @@ __global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ C
       issue(tile + gridDim.x);
       pending = true;
     }
-    const int dq = 32 * db + lane;
+    const int dq = 32 * q + lane;
     const float2 e_bcd = cscale(cmul(cconj(eo[bq]), cmul(eo[cq], eo[dq])), p.scale);
     float2* Wt = p.W + ((size_t)bq * N + cq) * N + dq;
 #pragma unroll
