@@ -101,8 +101,9 @@ struct pw_csd {
   int adj_iP, adj_jP;
   const pw::GradEpi* adj_grad;  // non-null: reduce the GSM parameter gradients in pass B (W_GRAD)
   CUtensorMap vmap;  // TMA map of the work buffer in the V layout
-  CUtensorMap ymap;  // N = 256: the second pass's tiles of Y1 (work buffer)
+  CUtensorMap ymap;  // N = 256: the second pass's tiles of the work buffer
   CUtensorMap y3map;  // N = 256: the third pass's tiles of the work buffer
+  CUtensorMap y1map;  // N = 256: the first pass's stores (four rows per warp) into the work buffer
   int dft_mode;      // PW_DFT_AUTO, PW_DFT_FP32 or PW_DFT_TC_BF16X3
   int Nz;            // zero padding: transform size (0 = none); the dense path runs when set
   void* qbuf;        // split DFT matrices of the tensor-core dense path (allocated on first use)
@@ -414,10 +415,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-// N = 256 (three-pass engine): Y[a][b][k_l][d' / 8][r][d' mod 8] in the work buffer as floats
+// N = 256 (three-pass engine): Y[a][b][k_l'][d' / 8][r][d' mod 8] in the work buffer as floats
 // {64, 32, 64, N, N} (the innermost 64 floats are one 256-byte run of 4 r x 8 d'), with the second
 // pass's box {64, 1, 1, N, 1} (one run for every b) and the third pass's box {16, 4, 1, 1, N} (the
-// 64-byte pieces of one k_h in four consecutive runs, for every a).
+// 64-byte pieces of one k_h in four consecutive runs, for every a); the first pass stores through
+// the same array as floats {16, 4, 32, 64, N^2} with box {16, 1, 32, 4, 1} (four k_l' rows of
+// one r: 128 pieces of 64 bytes).
 pw_status make_t256_maps(pw_csd* h) {
   auto enc = encode_tiled();
   if (!enc) return fail(PW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -434,6 +437,14 @@ pw_status make_t256_maps(pw_csd* h) {
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (third-pass tiles) failed (CUresult %d)", (int)r);
+  {
+    const cuuint64_t d1[5] = {16, 4, 32, 64, N * N};
+    const cuuint64_t s1[4] = {64, 256, 256 * 32, 256 * 32 * 64};
+    const cuuint32_t b1[5] = {16, 1, 32, 4, 1};
+    r = enc(&h->y1map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, h->work, d1, s1, b1, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PW_ECUDA, "cuTensorMapEncodeTiled (first-pass rows) failed (CUresult %d)", (int)r);
+  }
   return PW_OK;
 }
 
@@ -640,7 +651,7 @@ pw_status propagate_t256(pw_csd* h, double z, bool herm) {
       if (r != cudaSuccess) return r;
       ready = true;
     }
-    k<<<num_sms(), T::NT1, T::pass1_smem(), h->stream>>>(a, reinterpret_cast<float2*>(h->work));
+    k<<<num_sms(), T::NT1, T::pass1_smem(), h->stream>>>(h->y1map, a);
     return cudaGetLastError();
   };
   static bool ready1[4] = {false, false, false, false};

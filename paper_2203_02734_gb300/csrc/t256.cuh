@@ -9,12 +9,12 @@
 // so the point-2 transform is a DFT-64 over m and a DFT-256 over d for each r (pass 1), then a
 // twiddle e^{-2 pi i r k_l / 256} and a DFT-4 over r (pass 2).  With d' = 8 g + j (j < 8) the
 // intermediate array lives in the work buffer as
-//   Y[a][b][k_l][g][r][j]  (after pass 1)  and  Y[a][b'][k_l][g][k_h][j]  (after pass 2),
-// so that the 4 x 8 values one pass-2 line group needs are one 256-byte run.
+//   Y[a][b][kperm(k_l)][g][r][j]  (after pass 1)  and  Y[a][b'][kperm(k_l)][g][k_h][j]  (after pass 2),
+// so that the 4 x 8 values one pass-2 line group needs are one 256-byte run (kperm: below).
 //   pass 1, tile (a, b, r): the source rows c = r + 4 m of slice (a, b) are generated in registers
 //     (W1(c, d) = conj F(a, b) F(c, d) x source), transformed over (m, d) as a 64 x 256 2D DFT in
-//     registers through one shared buffer, and stored to Y (64-byte pieces of the 256-byte runs;
-//     the four r tiles of a slice run side by side and fill each run together).
+//     registers through one shared buffer, and stored to Y by TMA (64-byte pieces of the 256-byte
+//     runs; the four r tiles of a slice run side by side and fill each run together).
 //   pass 2, tile (a, k_l, g): the 256 runs Y[a][.][k_l][g] (all b, r, j) arrive by one TMA tensor
 //     load; twiddle e^{-2 pi i r k_l / 256}, DFT-4 over r (-> k_h), DFT-256 over b (sign +1);
 //     stored back to the same runs (the tile reads and writes one set of addresses).
@@ -70,17 +70,23 @@ template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int
 //            (k_l, d') at the input positions;
 // (w_L = e^{-2 pi i / L}).  The two exchanges go through one 128 KB buffer whose column index is
 // XOR-swizzled per exchange so that every access of a warp touches each 8-byte bank pair twice:
-//   exchange 1: q ^ ((q >> 4) & 7);  exchange 2: q ^ (((q >> 6) & 3) << 3).
-// The outputs go to Y[a][b][k_l][d' / 8][r][d' mod 8] straight from registers (each warp store is
-// four 64-byte pieces); the twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue
-// slots to spare.
+//   exchange 1: q ^ ((q >> 4) & 7);  exchange 2: q ^ (((q >> 6) & 3) << 3);
+// exchange 2 also permutes the rows (logical row p at buffer row kperm(p)), so that the rows of a
+// stage-3 warp are adjacent.  Stage 3 writes its outputs back over its own rows in natural order and
+// each warp leaves its four rows by one TMA tensor store into Y[a][b][kperm(k_l)][d' / 8][r][d' mod 8];
+// the next tile's first exchange waits (per warp, before the block barrier) until those stores have
+// read the buffer.  The twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue slots
+// to spare.
+// Position of k_l along the k_l index of Y: the four rows k_l = w + 16 i that stage 3 of warp w
+// owns are adjacent (4 w + i), so that one TMA store moves them.
+__device__ __forceinline__ int kperm(int kl) { return 4 * (kl & 15) + (kl >> 4); }
 __device__ __forceinline__ int xs1(int q) { return q ^ ((q >> 4) & 7); }
 __device__ __forceinline__ int xs2(int q) { return q ^ (((q >> 6) & 3) << 3); }
 
 constexpr size_t pass1_smem() { return (size_t)64 * N * sizeof(float2) + N * sizeof(float2); }
 
 template <int SRC>
-__global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __restrict__ Y1) {
+__global__ void __launch_bounds__(NT1, 1) pass1_kernel(const __grid_constant__ CUtensorMap smap, PassAArgs p) {
   constexpr bool ARRAY = SRC == SRC_ARRAY, DIAG = SRC == SRC_DIAG;
   extern __shared__ __align__(1024) float2 smem[];
   float2* buf = smem;  // 64 x 256
@@ -120,7 +126,18 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __re
         v[rp][rq] = x;
       }
     }
-    r128::dft2d<4, 8, -1>(v);
+#pragma unroll
+    for (int rp = 0; rp < 4; ++rp) Dft<8, -1>::run(v[rp]);  // rows first: the first rows' DFTs overlap later loads
+#pragma unroll
+    for (int rq = 0; rq < 8; ++rq) {
+      float2 cc[4];
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp) cc[rp] = v[rp][rq];
+      Dft<4, -1>::run(cc);
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp) v[rp][rq] = cc[rp];
+    }
+    if (lane == 0) bulk_wait_read_all();  // this warp's row stores of the previous tile have left buf
     __syncthreads();  // tw (first tile); every read of buf of the previous tile is done
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp)
@@ -138,25 +155,37 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(PassAArgs p, float2* __re
     for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
       for (int rq = 0; rq < 8; ++rq)
-        buf[(16 * (w >> 2) + (w & 3) + 4 * rp) * N + xs2(64 * (lane >> 3) + (lane & 7) + 8 * rq)] = v[rp][rq];
+        buf[(4 * ((w & 3) + 4 * rp) + (w >> 2)) * N + xs2(64 * (lane >> 3) + (lane & 7) + 8 * rq)] = v[rp][rq];
     __syncthreads();
-    float2* Ys = Y1 + (size_t)ab * N * N + 8 * r;
+    // stage 3 on the warp's own rows k_l = w + 16 rp (buffer rows 4 w + rp): read both halves,
+    // transform, write the outputs back in natural order, then one TMA store of the four rows
+    // (4 x 32 pieces of 64 bytes into Y), which drains while the next tile's stage 1 runs
+    float2 u[2][4][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+        for (int rq = 0; rq < 4; ++rq) u[h][rp][rq] = buf[(4 * w + rp) * N + xs2(lane + 32 * h + 64 * rq)];
+    __syncwarp();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int jq = lane + 32 * h;
-      float2 u[4][4];
+      r128::twiddle2d<4, 4, -1>(u[h], tw, 4 * w, jq);
+      r128::dft2d<4, 4, -1>(u[h]);
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-        for (int rq = 0; rq < 4; ++rq) u[rp][rq] = buf[(w + 16 * rp) * N + xs2(jq + 64 * rq)];
-      r128::twiddle2d<4, 4, -1>(u, tw, 4 * w, jq);
-      r128::dft2d<4, 4, -1>(u);
-#pragma unroll
-      for (int rp = 0; rp < 4; ++rp)
-#pragma unroll
-        for (int rq = 0; rq < 4; ++rq) Ys[(w + 16 * rp) * 1024 + (jq >> 3) * 32 + (jq & 7) + 256 * rq] = u[rp][rq];
+        for (int rq = 0; rq < 4; ++rq) buf[(4 * w + rp) * N + jq + 64 * rq] = u[h][rp][rq];
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_5d(&smap, buf + 4 * w * N, 0, r, 0, 4 * w, ab);  // rows k_l' = 4 w + rp (k_l = w + 16 rp)
+      bulk_commit();
     }
   }
+  if (lane == 0) bulk_wait_all();
 }
 
 // Bounded wait on the tile load of a pass-2/3 CTA; every thread learns the outcome.  A wait that
@@ -172,14 +201,14 @@ __device__ __forceinline__ bool tile_arrived(uint64_t* mbar, uint32_t parity, in
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pass 2.  Tile (a, k_l, g): X[b][r][j] = Y[a][b][k_l][g][r][j] (b < 256, r < 4, j < 8), 64 KB by
-// one TMA load (tensor map: Y as floats {64, 32, 64, 256, 256}, box {64, 1, 1, 256, 1}).
+// Pass 2.  Tile (a, k_l, g): X[b][r][j] = Y[a][b][kperm(k_l)][g][r][j] (b < 256, r < 4, j < 8),
+// 64 KB by one TMA load (tensor map: Y as floats {64, 32, 64, 256, 256}, box {64, 1, 1, 256, 1}).
 //   phase 1: twiddle e^{-2 pi i r k_l / 256} and DFT-4 over r (sign -1) for each (b, j), in place
 //            (r -> k_h);
 //   phase 2: DFT-256 over b (sign +1), first radix-16 stage: line L = (k_h, j) = lane, butterflies
 //            n1 = w and w + 8, inputs b = n1 + 16 n2, twiddle w256^(n1 k2), in place;
 //   phase 3: second stage: butterflies k2 = w, w + 8, inputs n1 + 16 k2, outputs b' = k2 + 16 k1.
-// Outputs go back to the runs they came from, Y[a][b'][k_l][g][k_h][j] (line L = 8 k_h + j = lane:
+// Outputs go back to the runs they came from, Y[a][b'][kperm(k_l)][g][k_h][j] (line L = 8 k_h + j = lane:
 // one 256-byte run per warp store).  The next tile's load is issued once every thread has read the
 // buffer.
 constexpr size_t pass2_smem() { return (size_t)N * 4 * 8 * sizeof(float2) + N * sizeof(float2) + 64; }
@@ -197,7 +226,7 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
     const int db = tile & 31, kl = (tile >> 5) & 63, a = tile >> 11;
     fence_proxy_async_smem();
     mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
-    tma_load_5d(X, &ymap, mbar, 0, db, kl, 0, a);
+    tma_load_5d(X, &ymap, mbar, 0, db, kperm(kl), 0, a);
   };
   bool pending = false;  // thread 0: a load was issued and not yet seen complete
   if (t == 0) {
@@ -256,7 +285,7 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
       issue(tile + gridDim.x);
       pending = true;
     }
-    float2* Ya = Y + (size_t)a * N * N * N + kl * 1024 + db * 32 + lane;
+    float2* Ya = Y + (size_t)a * N * N * N + kperm(kl) * 1024 + db * 32 + lane;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int k2 = w + 8 * e;
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(NT2, 2) pass2_kernel(const __grid_constant__ C
 
 // ---------------------------------------------------------------------------------------------
 // Pass 3.  Tile (k_h, q, k_l, b'), k_h fastest: c' = k_l + 64 k_h, d' = 32 q + j,
-// X[a][j] = Y[a][b'][k_l][4 q + j / 8][k_h][j mod 8] (a < 256, j < 32), 64 KB by one TMA load
+// X[a][j] = Y[a][b'][kperm(k_l)][4 q + j / 8][k_h][j mod 8] (a < 256, j < 32), 64 KB by one TMA load
 // (tensor map: Y as floats {64, 32, 64, 256, 256}, box {16, 4, 1, 1, 256}).  DFT-256 over a (sign
 // +1) as two radix-16 stages (line j = lane; butterflies 2 w, 2 w + 1), then the epilogue
 // W_B = s conj(E(a') E(b')) E(c') E(d') X and S on the diagonal, stored to W[a'][b'][c'][d'].
@@ -293,7 +322,7 @@ __global__ void __launch_bounds__(NT2, 2) pass3_kernel(const __grid_constant__ C
     const int kh = tile & 3, q = (tile >> 2) & 7, kl = (tile >> 5) & 63, bq = tile >> 11;
     fence_proxy_async_smem();
     mbar_expect(mbar, (uint32_t)(N * 32 * sizeof(float2)));
-    tma_load_5d(X, &y3map, mbar, 16 * kh, 4 * q, kl, bq, 0);
+    tma_load_5d(X, &y3map, mbar, 16 * kh, 4 * q, kperm(kl), bq, 0);
   };
   bool pending = false;  // thread 0: a load was issued and not yet seen complete
   if (t == 0) {
