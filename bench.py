@@ -631,6 +631,7 @@ def run_batch(args):
     e1.record()
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1) / reps
+    peak, peak_src = measured_peak_hbm()
     for h in hl.values():
         pw.pw_csd_destroy(h)
     pw.pw_batch_destroy(b)
@@ -641,6 +642,10 @@ def run_batch(args):
                        "Ns": list(CFG["Ns"]), "zs": list(CFG["zs"]), "n_freq": CFG["n_freq"],
                        "outputs": "S and mu per instance", "pool": pool, "chunk": chunk,
                        "launch": "autotuned mode: %s, replayed from a CUDA graph" % mode},
+            "roofline": {"bound": "hbm", "kernel": "whole batch (V written by pass A, read by the S/mu pass)",
+                         "achieved": 16.0 * pts / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": 16.0 * pts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src, "traffic": None,
+                         "algorithmic_bytes_per_point": 16},
             "plain_path": {"value": pts / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                            "what": "the same instances through the single-instance calls, one after another"},
             "gpu_launches": (4 if mode.startswith("persistent") else 2 + 2 * len(specs)) * args.steps,

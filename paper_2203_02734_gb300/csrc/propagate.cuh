@@ -478,4 +478,83 @@ static __global__ void s_mu_kernel(SMuArgs a) {
   }
 }
 
+// S and the P1 row of one propagation from V alone, for callers that keep no W (the batch).  Of
+// the sign-+1 2D DFT over x1 = (a, b) that pass B runs on column x2 = (c, d), only two outputs are
+// used: (a', b') = (c, d) for S and (a', b') = P1 for the mu numerator.  Each is one dot product
+//   X(a', b') = sum_{a,b} e^{+2 pi i (a a' + b b') / N} V(a, b; c, d)
+// with a separable phase, so V is streamed in its own layout V[c][d/4][a][b][d mod 4]: one block of
+// 4 N^2 contiguous values per (c, d/4), four columns, no gather.  Thread t owns the (b, j) pairs
+// k = t + 256 s of every a-row (j = d mod 4 = t mod 4), sums over a with e^{+2 pi i a c / N} and
+// e^{+2 pi i a iP / N}, then applies the b phase and the block reduces over b.  The epilogue is
+// pass B's: W(a', b'; c, d) = s conj(E(a') E(b')) E(c) E(d) X(a', b').
+template <int N>
+__global__ void __launch_bounds__(256) smu_from_v_kernel(PassBArgs p) {
+  constexpr int G = 4, ROW = N * G, SLOTS = (ROW + 255) / 256, NG = N * N / G;
+  __shared__ float2 phc[N], php[N];
+  __shared__ float2 red[8][4][2];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, j = t & 3;
+  const bool row = p.row != nullptr;
+  for (int q = blockIdx.x; q < NG; q += gridDim.x) {
+    const int c = q / (N / G), dg = q - c * (N / G);
+    __syncthreads();  // the previous group's tables and partial sums are consumed
+    for (int a = t; a < N; a += 256) {
+      phc[a] = cconj(__ldg(p.tw + (a * c) % N));
+      php[a] = cconj(__ldg(p.tw + (a * p.iP) % N));
+    }
+    __syncthreads();
+    const float2* __restrict__ Vq = p.V + (size_t)q * N * ROW;
+    float2 ad[SLOTS], ap[SLOTS];
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) ad[s] = ap[s] = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int a = 0; a < N; ++a) {
+      const float2 pc = phc[a], pp = php[a];
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int k = t + 256 * s;
+        if (ROW % 256 == 0 || k < ROW) {
+          const float2 v = __ldg(Vq + a * ROW + k);
+          ad[s] = cadd(ad[s], cmul(pc, v));
+          ap[s] = cadd(ap[s], cmul(pp, v));
+        }
+      }
+    }
+    float2 sd = make_float2(0.f, 0.f), sp = make_float2(0.f, 0.f);
+    const int d = G * dg + j;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int k = t + 256 * s, b = k >> 2;
+      if (ROW % 256 == 0 || k < ROW) {
+        sd = cadd(sd, cmul(cconj(__ldg(p.tw + (b * d) % N)), ad[s]));
+        sp = cadd(sp, cmul(cconj(__ldg(p.tw + (b * p.jP) % N)), ap[s]));
+      }
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      sd.x += __shfl_xor_sync(0xffffffffu, sd.x, o);
+      sd.y += __shfl_xor_sync(0xffffffffu, sd.y, o);
+      sp.x += __shfl_xor_sync(0xffffffffu, sp.x, o);
+      sp.y += __shfl_xor_sync(0xffffffffu, sp.y, o);
+    }
+    if (lane < 4) {
+      red[warp][lane][0] = sd;
+      red[warp][lane][1] = sp;
+    }
+    __syncthreads();
+    if (t < 4) {
+      float2 xd = make_float2(0.f, 0.f), xp = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        xd = cadd(xd, red[w][t][0]);
+        xp = cadd(xp, red[w][t][1]);
+      }
+      const int dd = G * dg + t, cd = c * N + dd;
+      const float2 ecd = cscale(cmul(__ldg(p.Eout + c), __ldg(p.Eout + dd)), p.scale);
+      const float2 wd = cmul(cmul(cmul(cconj(__ldg(p.Eout + c)), ecd), cconj(__ldg(p.Eout + dd))), xd);
+      p.S[cd] = wd.x;
+      if (row) p.row[cd] = cmul(cmul(cmul(cconj(__ldg(p.Eout + p.iP)), ecd), cconj(__ldg(p.Eout + p.jP))), xp);
+    }
+  }
+}
+
 }  // namespace pw
