@@ -301,28 +301,53 @@ struct PassBArgs {
 // (W_GRAD) nothing but the GSM parameter-gradient sums of the adjoint.
 enum WStore { W_NONE = 0, W_HERM = 1, W_GENERAL = 2, W_GRAD = 3 };
 
-// Per-thread FP32 sums of the W_GRAD epilogue for one column x2 = (c, d).
+// W_GRAD epilogue for one column x2 = (c, d).  With R = Re(W_B conj-factors) the per-point terms
+//   t = R G(a, c) G(b, d) m(a, b),  sum t r^2,  sum t |x1 - x2|^2,  sum t
+// are separable in a and b: r^2 = (a-M)^2 + (b-M)^2 + (c-M)^2 + (d-M)^2 and |x1 - x2|^2 =
+// (a-c)^2 + (b-d)^2, so each point-1 index carries its own G factor, squares and output factor
+// (GradAxis), set up once per row / column of the thread; the column's (c-M)^2 + (d-M)^2 enters
+// in grad_reduce.  In the far field W_B is also multiplied by q(a) q(b) conj(q(c) q(d)), folded
+// into the same factors (grad_col for the column part).
+struct GradAxis {
+  float g, r, dd;  // G(a, c), (a - M)^2, (a - c)^2
+  float2 e;        // output factor of this index (times q(a) in the far field)
+};
+__device__ __forceinline__ GradAxis grad_axis(const GradEpi& g, int N, int a, int c, float2 e) {
+  GradAxis x;
+  x.g = __ldg(g.gtab + a * N + c);
+  const float m = (float)(a - N / 2), dd = (float)(a - c);
+  x.r = m * m;
+  x.dd = dd * dd;
+  x.e = g.qff ? cmul(e, __ldg(g.qff + a)) : e;
+  return x;
+}
+// the column factor s E(c) E(d) (times conj(q(c) q(d)) in the far field)
+__device__ __forceinline__ float2 grad_col(const GradEpi& g, int c, int d, float2 ecd) {
+  return g.qff ? cmul(ecd, cconj(cmul(__ldg(g.qff + c), __ldg(g.qff + d)))) : ecd;
+}
 struct GradSums {
-  float sS = 0.f, sM = 0.f, sA = 0.f;
-  // the output value R(x1, x2) at x1 = (a, b), x2 = (c, d); N / 2 = M
-  __device__ __forceinline__ void add(const GradEpi& g, int N, int a, int b, int c, int d, float2 w) {
-    if (g.qff) w = cmul(w, cmul(cmul(__ldg(g.qff + a), __ldg(g.qff + b)), cconj(cmul(__ldg(g.qff + c), __ldg(g.qff + d)))));
-    float t = w.x * __ldg(g.gtab + a * N + c) * __ldg(g.gtab + b * N + d);
-    if (g.amask) t *= __ldg(g.amask + a * N + b);
-    const int M = N / 2;
-    const float r2 = (float)((a - M) * (a - M) + (M - b) * (M - b) + (c - M) * (c - M) + (M - d) * (M - d));
-    const float dx2 = (float)((a - c) * (a - c) + (b - d) * (b - d));
-    sS = fmaf(t, r2, sS);
-    sM = fmaf(t, dx2, sM);
+  float sS = 0.f, sM = 0.f, sA = 0.f;  // sS without the column's (c-M)^2 + (d-M)^2 (grad_reduce)
+  // transform value y at x1 = (a, b) (axis factors A of a, B of b; m = mask value m(a, b))
+  __device__ __forceinline__ void add(const GradAxis& A, const GradAxis& B, float m, float2 y) {
+    const float2 e = cmul(A.e, B.e);
+    const float t = (e.x * y.x - e.y * y.y) * (A.g * B.g) * m;
+    sS = fmaf(t, A.r + B.r, sS);
+    sM = fmaf(t, A.dd + B.dd, sM);
     sA += t;
   }
 };
+__device__ __forceinline__ float grad_mask(const GradEpi& g, int N, int a, int b) {
+  return g.amask ? __ldg(g.amask + a * N + b) : 1.f;
+}
 
 // Block reduction of the W_GRAD sums of column cd (red: 4 x 32 doubles of shared memory); writes
 // part[cd] and gmask[cd].  Every thread of the block must call it.
 __device__ __forceinline__ void grad_reduce(const GradEpi& g, int N, int cd, const GradSums& s, double* red) {
   const float a2 = g.amask ? __ldg(g.amask + cd) : 1.f;
-  double v[4] = {(double)s.sS * a2 * g.d2, (double)s.sM * a2 * g.d2, (double)s.sA * a2, (double)s.sA};
+  const int c = cd / N, d = cd - c * N;
+  const float rc = (float)((c - N / 2) * (c - N / 2) + (d - N / 2) * (d - N / 2));
+  const float sS = fmaf(rc, s.sA, s.sS);
+  double v[4] = {(double)sS * a2 * g.d2, (double)s.sM * a2 * g.d2, (double)s.sA * a2, (double)s.sA};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -403,9 +428,10 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
     } else if constexpr (WST == W_GRAD) {
       GradSums gs;
       const GradEpi& ge = p.gr;
+      const float2 ecg = grad_col(ge, c, d, ecd);
       auto epi = [&](int a, int b, float2 y) {
-        const float2 w = cmul(cmul(cconj(cmul(eo[a], eo[b])), ecd), y);
-        gs.add(ge, N, a, b, c, d, w);
+        gs.add(grad_axis(ge, N, a, c, cmul(cconj(eo[a]), ecg)), grad_axis(ge, N, b, d, cconj(eo[b])),
+               grad_mask(ge, N, a, b), y);
       };
       fft_stage<N, StageInfo<N, S - 1>::R, StageInfo<N, S - 1>::NS, +1, true, NT>(tw, ld0, NoMid{}, epi);
       grad_reduce(ge, N, cd, gs, red);

@@ -371,28 +371,41 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
     float2* Wrow = p.W + (size_t)cd * N * N;
     float2* rw = p.row;
     const int iP = p.iP, jP = p.jP;
-    GradSums gs;
+    if constexpr (WST == W_GRAD) {
+      GradSums gs;
+      const float2 ecg = grad_col(p.gr, c, d, ecd);
+      GradAxis B[4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+      for (int rq = 0; rq < 4; ++rq) B[rq] = grad_axis(p.gr, N, lane + 32 * rq, d, cconj(eo[lane + 32 * rq]));
 #pragma unroll
-      for (int rp = 0; rp < 4; ++rp) {
-        const int a = warp + 16 * i + 32 * rp;
-        const float2 ea = cmul(cconj(eo[a]), ecd);
+      for (int i = 0; i < 2; ++i) {
 #pragma unroll
-        for (int rq = 0; rq < 4; ++rq) {
-          const int b = lane + 32 * rq;
-          const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
-          if (WST == W_GRAD) {
-            gs.add(p.gr, N, a, b, c, d, w);
-            continue;
+        for (int rp = 0; rp < 4; ++rp) {
+          const int a = warp + 16 * i + 32 * rp;
+          const GradAxis A = grad_axis(p.gr, N, a, c, cmul(cconj(eo[a]), ecg));
+#pragma unroll
+          for (int rq = 0; rq < 4; ++rq) gs.add(A, B[rq], grad_mask(p.gr, N, a, lane + 32 * rq), w3[i][rp][rq]);
+        }
+      }
+      grad_reduce(p.gr, N, cd, gs, red);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int rp = 0; rp < 4; ++rp) {
+          const int a = warp + 16 * i + 32 * rp;
+          const float2 ea = cmul(cconj(eo[a]), ecd);
+#pragma unroll
+          for (int rq = 0; rq < 4; ++rq) {
+            const int b = lane + 32 * rq;
+            const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][rp][rq]);
+            if (a == c && b == d) p.S[cd] = w.x;
+            if (ROW && a == iP && b == jP) rw[cd] = w;
+            if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
           }
-          if (a == c && b == d) p.S[cd] = w.x;
-          if (ROW && a == iP && b == jP) rw[cd] = w;
-          if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
         }
       }
     }
-    if (WST == W_GRAD) grad_reduce(p.gr, N, cd, gs, red);
   }
   cp_async_wait_all();
 }

@@ -260,29 +260,43 @@ __global__ void __launch_bounds__(NT, 2) pass_b_r96(PassBArgs p) {
     stages<+1>(v, w3, X, tw);
     const float2 ecd = cscale(cmul(eo[c], eo[d]), p.scale);
     float2* Wrow = p.W + (size_t)cd * NN;
-    GradSums gs;
+    if constexpr (WST == W_GRAD) {
+      GradSums gs;
+      const float2 ecg = grad_col(p.gr, c, d, ecd);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int u = t + NT * i, jq = u % 24, jp = u / 24;
+      for (int i = 0; i < 3; ++i) {
+        const int u = t + NT * i, jq = u % 24, jp = u / 24;
+        GradAxis B[4];
 #pragma unroll
-      for (int kp = 0; kp < 4; ++kp) {
-        const int a = jp + 24 * kp;
-        const float2 ea = cmul(cconj(eo[a]), ecd);
+        for (int kq = 0; kq < 4; ++kq) B[kq] = grad_axis(p.gr, N, jq + 24 * kq, d, cconj(eo[jq + 24 * kq]));
 #pragma unroll
-        for (int kq = 0; kq < 4; ++kq) {
-          const int b = jq + 24 * kq;
-          const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][kp][kq]);
-          if (WST == W_GRAD) {
-            gs.add(p.gr, N, a, b, c, d, w);
-            continue;
+        for (int kp = 0; kp < 4; ++kp) {
+          const int a = jp + 24 * kp;
+          const GradAxis A = grad_axis(p.gr, N, a, c, cmul(cconj(eo[a]), ecg));
+#pragma unroll
+          for (int kq = 0; kq < 4; ++kq) gs.add(A, B[kq], grad_mask(p.gr, N, a, jq + 24 * kq), w3[i][kp][kq]);
+        }
+      }
+      grad_reduce(p.gr, N, cd, gs, red);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int u = t + NT * i, jq = u % 24, jp = u / 24;
+#pragma unroll
+        for (int kp = 0; kp < 4; ++kp) {
+          const int a = jp + 24 * kp;
+          const float2 ea = cmul(cconj(eo[a]), ecd);
+#pragma unroll
+          for (int kq = 0; kq < 4; ++kq) {
+            const int b = jq + 24 * kq;
+            const float2 w = cmul(cmul(ea, cconj(eo[b])), w3[i][kp][kq]);
+            if (a == c && b == d) p.S[cd] = w.x;
+            if (ROW && a == iP && b == jP) rw[cd] = w;
+            if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
           }
-          if (a == c && b == d) p.S[cd] = w.x;
-          if (ROW && a == iP && b == jP) rw[cd] = w;
-          if (WST == W_HERM) Wrow[a * N + b] = cconj(w);
         }
       }
     }
-    if (WST == W_GRAD) grad_reduce(p.gr, N, cd, gs, red);
   }
 }
 
