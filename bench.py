@@ -695,6 +695,39 @@ def run_adjoint(args):
     t1 = time.time()
     clocks = clock.stop(t0, t1)
     t_f = timed(fwd, args.steps)
+    # device time of the forward (S, mu) and of the adjoint call alone: CUDA events around the library
+    # calls, no host synchronisation inside (the autograd step above copies the three parameter
+    # gradients back to host tensors, which synchronises every step)
+    from paper_2203_02734_gb300 import abi
+    m = model.m
+    model.mask_c.real.copy_(am.detach())
+    gS_dev = torch.randn(N, N, device="cuda", dtype=torch.float32)
+
+    def dev_fwd():
+        abi.pw_csd_reset(m.csd.h, m.dxi)
+        abi.pw_source_gsm(m.csd.h, CFG["sigma_S"], CFG["sigma_mu"], 1.0)
+        abi.pw_source_mask(m.csd.h, model.mask_c.data_ptr())
+        m.propagate_and_read()
+
+    def dev_bwd():
+        m.adjoint(gS_dev, None, m.S, m.mu, sigma_S_m=CFG["sigma_S"], sigma_mu_m=CFG["sigma_mu"], amplitude=1.0,
+                  dev_amask=am.data_ptr(), dev_grad3=m.g3.data_ptr(), dev_grad_amask=m.gmask.data_ptr())
+
+    def dev_timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    nd = max(args.steps, 50)
+    d_f = dev_timed(dev_fwd, nd)
+    d_b = dev_timed(dev_bwd, nd)
     model.close()
     pts = N ** 4
     line = {"metric": METRIC, "value": pts / t_fb, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -704,6 +737,8 @@ def run_adjoint(args):
                        "step": "forward S + backward of a least-squares S loss (hand-written adjoint)"},
             "plain_path": {"value": pts / t_f, "unit": UNIT, "ms_per_step": 1e3 * t_f,
                            "what": "the forward propagation + S alone"},
+            "device": {"forward_ms": d_f, "backward_ms": d_b, "backward_over_forward": d_b / d_f,
+                       "what": "CUDA-event time of the forward (S, mu) and of one adjoint call, %d calls each" % nd},
             "gpu_launches": 7 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
 

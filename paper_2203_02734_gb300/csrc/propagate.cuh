@@ -509,21 +509,25 @@ static __global__ void s_mu_kernel(SMuArgs a) {
 // used: (a', b') = (c, d) for S and (a', b') = P1 for the mu numerator.  Each is one dot product
 //   X(a', b') = sum_{a,b} e^{+2 pi i (a a' + b b') / N} V(a, b; c, d)
 // with a separable phase, so V is streamed in its own layout V[c][d/4][a][b][d mod 4]: one block of
-// 4 N^2 contiguous values per (c, d/4), four columns, no gather.  Thread t owns the (b, j) pairs
-// k = t + 256 s of every a-row (j = d mod 4 = t mod 4), sums over a with e^{+2 pi i a c / N} and
-// e^{+2 pi i a iP / N}, then applies the b phase and the block reduces over b.  The epilogue is
+// 4 N^2 contiguous values per (c, d/4), four columns, no gather.  The block has one thread per value
+// of an a-row (4 N, at most 512; SMU_SLOTS rows' worth otherwise): thread t owns the (b, j) pairs
+// k = t + SMU_NT s (j = d mod 4 = t mod 4), sums over a with e^{+2 pi i a c / N} and
+// e^{+2 pi i a iP / N}, then applies the b phase, and the block reduces over b.  The epilogue is
 // pass B's: W(a', b'; c, d) = s conj(E(a') E(b')) E(c) E(d) X(a', b').
+template <int N> __host__ __device__ constexpr int smu_nt() { return 4 * N < 512 ? 4 * N : 512; }
+
 template <int N>
-__global__ void __launch_bounds__(256) smu_from_v_kernel(PassBArgs p) {
-  constexpr int G = 4, ROW = N * G, SLOTS = (ROW + 255) / 256, NG = N * N / G;
+__global__ void __launch_bounds__(smu_nt<N>()) smu_from_v_kernel(PassBArgs p) {
+  constexpr int G = 4, ROW = N * G, NT = smu_nt<N>(), SLOTS = ROW / NT, NW = NT / 32, NG = N * N / G;
+  static_assert(ROW % NT == 0 && NT % 32 == 0, "a-rows split evenly over the block");
   __shared__ float2 phc[N], php[N];
-  __shared__ float2 red[8][4][2];
+  __shared__ float2 red[NW][4][2];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, j = t & 3;
   const bool row = p.row != nullptr;
   for (int q = blockIdx.x; q < NG; q += gridDim.x) {
     const int c = q / (N / G), dg = q - c * (N / G);
     __syncthreads();  // the previous group's tables and partial sums are consumed
-    for (int a = t; a < N; a += 256) {
+    for (int a = t; a < N; a += NT) {
       phc[a] = cconj(__ldg(p.tw + (a * c) % N));
       php[a] = cconj(__ldg(p.tw + (a * p.iP) % N));
     }
@@ -537,23 +541,18 @@ __global__ void __launch_bounds__(256) smu_from_v_kernel(PassBArgs p) {
       const float2 pc = phc[a], pp = php[a];
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
-        const int k = t + 256 * s;
-        if (ROW % 256 == 0 || k < ROW) {
-          const float2 v = __ldg(Vq + a * ROW + k);
-          ad[s] = cadd(ad[s], cmul(pc, v));
-          ap[s] = cadd(ap[s], cmul(pp, v));
-        }
+        const float2 v = __ldg(Vq + a * ROW + t + NT * s);
+        ad[s] = cadd(ad[s], cmul(pc, v));
+        ap[s] = cadd(ap[s], cmul(pp, v));
       }
     }
     float2 sd = make_float2(0.f, 0.f), sp = make_float2(0.f, 0.f);
     const int d = G * dg + j;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      const int k = t + 256 * s, b = k >> 2;
-      if (ROW % 256 == 0 || k < ROW) {
-        sd = cadd(sd, cmul(cconj(__ldg(p.tw + (b * d) % N)), ad[s]));
-        sp = cadd(sp, cmul(cconj(__ldg(p.tw + (b * p.jP) % N)), ap[s]));
-      }
+      const int b = (t + NT * s) >> 2;
+      sd = cadd(sd, cmul(cconj(__ldg(p.tw + (b * d) % N)), ad[s]));
+      sp = cadd(sp, cmul(cconj(__ldg(p.tw + (b * p.jP) % N)), ap[s]));
     }
 #pragma unroll
     for (int o = 4; o < 32; o <<= 1) {
@@ -570,7 +569,7 @@ __global__ void __launch_bounds__(256) smu_from_v_kernel(PassBArgs p) {
     if (t < 4) {
       float2 xd = make_float2(0.f, 0.f), xp = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int w = 0; w < 8; ++w) {
+      for (int w = 0; w < NW; ++w) {
         xd = cadd(xd, red[w][t][0]);
         xp = cadd(xp, red[w][t][1]);
       }

@@ -827,15 +827,15 @@ cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::Pass
   cudaError_t e;
   // Without W (S and the P1 row only) the second pass is smu_from_v_kernel: two dot products per
   // column instead of the full DFT over point 1, reading V in its own layout.
-  auto smu = [&](auto k, int groups) -> cudaError_t {
-    k<<<std::min(groups, num_sms() * 6), 256, 0, s>>>(b);
+  auto smu = [&](auto k, int groups, int nt) -> cudaError_t {
+    k<<<std::min(groups, num_sms() * (2048 / nt)), nt, 0, s>>>(b);
     return cudaGetLastError();
   };
   switch (N) {
 #define PW_BCASE(NN)                                                                                        \
   case NN:                                                                                                  \
     if ((e = launch_a_mode<NN, pw::SRC_GSM>(vmap, a, x, s)) != cudaSuccess) return e;                       \
-    if (!b.W) return smu(pw::smu_from_v_kernel<NN>, NN * NN / 4);                                           \
+    if (!b.W) return smu(pw::smu_from_v_kernel<NN>, NN * NN / 4, pw::smu_nt<NN>());                        \
     if constexpr (NN == 128) return launch_b_r128<pw::W_HERM, true>(b, s);                                 \
     else if constexpr (NN == 96) return launch_b_r96<pw::W_HERM, true>(b, s);                              \
     else return launch_b<NN, pw::W_HERM, true>(b, s);
