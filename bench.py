@@ -271,6 +271,10 @@ def roofline_dense(N, pts, avg_a, avg_b, clocks, tc):
                 "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src + " (bf16, burst)", "traffic": None,
                 "algorithmic_flops_per_launch": flops,
                 "fp32_equivalent_tflops": fp32_flops / (avg / 1e3) / 1e12,
+                # the method's own work (8 N flop per output point) against the split-BF16x3 ceiling:
+                # each FP32 product costs six BF16 products, so at most peak / 6 of FP32 work
+                "method_work": {"achieved": fp32_flops / (avg / 1e3) / 1e12, "ceiling": peak / 6.0,
+                                "frac": fp32_flops / (avg / 1e3) / 1e12 / (peak / 6.0), "unit": "TFLOP/s"},
                 "pass_ms": {"pass_a": avg_a, "pass_b": avg_b}}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
