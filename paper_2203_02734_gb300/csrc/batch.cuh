@@ -260,11 +260,13 @@ __device__ __noinline__ void item_a_r128(const Inst& in, int first, int count, i
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-        for (int rq = 0; rq < 4; ++rq) buf[(warp + 16 * i + 32 * rp) * N + lane + 32 * rq] = w3[i][rp][rq];
+        for (int rq = 0; rq < 4; ++rq)
+          buf[vrow<N>(warp + 16 * i + 32 * rp) * N + lane + 32 * rq] = w3[i][rp][rq];
     fence_proxy_async_smem();
     __syncthreads();
-    if (t == 0) {
-      tma_store_5d(vmap, buf, 0, b, a, 0, 0);
+    if (t == 0) {  // the tensor map's box is 8 rows of V (rows in vrow order)
+#pragma unroll 1
+      for (int r8 = 0; r8 < N; r8 += 8) tma_store_5d(vmap, buf + r8 * N, 0, b, a, 0, r8);
       bulk_commit();
     }
   }
@@ -316,7 +318,7 @@ __device__ __noinline__ void item_b_r128(const Inst& in, int first, int count, i
   auto prefetch = [&](int cdn) {
     if (t == 0 && cdn <= last) {
       const int cn = cdn / N, dn = cdn % N;
-      const float2* blk = V + (size_t)(cn * (N / g) + dn / g) * g * NN;
+      const float2* blk = V + (size_t)(vrow<N>(cn) * (N / g) + dn / g) * g * NN;
 #pragma unroll
       for (int j = 0; j < g; ++j) bulk_prefetch_l2(blk + (size_t)j * NN, (unsigned)(NN * sizeof(float2)));
     }

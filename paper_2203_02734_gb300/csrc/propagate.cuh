@@ -140,11 +140,15 @@ template <int N> __host__ __device__ constexpr int pitch() { return N + 1; }
 // drains in half the time (pass B's 8-byte gathers cost about the same either way).
 __host__ __device__ constexpr int vgroup_of(int n) { return n == 256 ? 8 : n % 4 == 0 ? 4 : 2; }
 template <int N> __host__ __device__ constexpr int vgroup() { return vgroup_of(N); }
+// Row of c' along V's c' index.  At N = 128 the eight rows c' = w + 16 i that one pass-A warp
+// finishes are adjacent (8 w + i), so that the warp leaves them by one TMA store; other N keep c'.
+template <int N> __host__ __device__ constexpr int vrow(int c) { return N == 128 ? 8 * (c & 15) + (c >> 4) : c; }
+template <int N> __host__ __device__ constexpr int vrow_inv(int r) { return N == 128 ? 16 * (r & 7) + (r >> 3) : r; }
 // offset of V(a, b, c', d') in the V layout
 template <int N>
 __device__ __forceinline__ size_t v_offset(int ab, int c, int d) {
   constexpr int g = vgroup<N>();
-  return (((size_t)(c * (N / g) + d / g) * (N * N) + ab) * g) + (d % g);
+  return (((size_t)(vrow<N>(c) * (N / g) + d / g) * (N * N) + ab) * g) + (d % g);
 }
 
 template <int N> __host__ __device__ constexpr size_t pass_a_smem() {
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 1) pass_b_kernel(PassBArgs p) {
   auto prefetch = [&](int cdn) {
     if (N >= 32 && threadIdx.x == 0 && cdn < N * N) {
       const int cn = cdn / N, dn = cdn % N;
-      bulk_prefetch_l2(p.V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
+      bulk_prefetch_l2(p.V + ((size_t)(vrow<N>(cn) * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
     }
   };
   prefetch(blockIdx.x);
@@ -509,7 +513,7 @@ static __global__ void s_mu_kernel(SMuArgs a) {
 // used: (a', b') = (c, d) for S and (a', b') = P1 for the mu numerator.  Each is one dot product
 //   X(a', b') = sum_{a,b} e^{+2 pi i (a a' + b b') / N} V(a, b; c, d)
 // with a separable phase, so V is streamed in its own layout V[c][d/4][a][b][d mod 4]: one block of
-// 4 N^2 contiguous values per (c, d/4), four columns, no gather.  The block has one thread per value
+// 4 N^2 contiguous values per (c, d/4) (row vrow(c)), four columns, no gather.  The block has one thread per value
 // of an a-row (4 N, at most 512; SMU_SLOTS rows' worth otherwise): thread t owns the (b, j) pairs
 // k = t + SMU_NT s (j = d mod 4 = t mod 4), sums over a with e^{+2 pi i a c / N} and
 // e^{+2 pi i a iP / N}, then applies the b phase, and the block reduces over b.  The epilogue is
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(smu_nt<N>()) smu_from_v_kernel(PassBArgs p) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, j = t & 3;
   const bool row = p.row != nullptr;
   for (int q = blockIdx.x; q < NG; q += gridDim.x) {
-    const int c = q / (N / G), dg = q - c * (N / G);
+    const int cr = q / (N / G), dg = q - cr * (N / G), c = vrow_inv<N>(cr);  // block q holds V row cr
     __syncthreads();  // the previous group's tables and partial sums are consumed
     for (int a = t; a < N; a += NT) {
       phc[a] = cconj(__ldg(p.tw + (a * c) % N));

@@ -806,8 +806,11 @@ pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
   const cuuint64_t run = (cuuint64_t)2 * g * sizeof(float);
   cuuint64_t dims[5] = {(cuuint64_t)2 * g, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)(N / g), (cuuint64_t)N};
   cuuint64_t strides[4] = {run, run * N, run * N * N, run * N * N * (N / g)};
+  // N = 256 (cluster engine): each CTA stores N / CLUSTER_A columns of the slice; N = 128: each
+  // warp stores its eight rows; otherwise the whole slice in one box
   const int cols = N == 256 ? N / pw::d256::CLUSTER_A : N;
-  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)N};
+  const int rows = N == 128 ? 8 : N;
+  cuuint32_t box[5] = {(cuuint32_t)(2 * g), 1, 1, (cuuint32_t)(cols / g), (cuuint32_t)rows};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, work, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,

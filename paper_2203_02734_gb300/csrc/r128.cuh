@@ -64,10 +64,13 @@ __device__ __forceinline__ void twiddle2d(float2 (&v)[RP][RQ], const float2* tw,
 
 // Stages 2 and 3 from stage-1 outputs v (already the thread's 8 x 4 block), through buf.
 // On return w3[i][rp][rq] holds the transform at (jp3 + 32 rp, lane + 32 rq), jp3 = warp + 16 i.
+// ROWS: the second exchange puts row p at buffer row vrow(p), so that the rows stage 3 of a warp
+// reads (c' = warp + 16 i + 32 rp) are the eight buffer rows 8 warp .. 8 warp + 7.
 // Contract: buf is free on entry (all threads passed a barrier after its last use).
-template <int SIGN>
+template <int SIGN, bool ROWS = false>
 __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][4], float2* buf,
                                          const float2* tw) {
+  auto row = [](int p) { return ROWS ? vrow<N>(p) : p; };
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 #pragma unroll
   for (int rp = 0; rp < 8; ++rp)
@@ -87,7 +90,7 @@ __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][
   for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
     for (int rq = 0; rq < 8; ++rq)
-      buf[((jp2 >> 3) * 32 + (jp2 & 7) + 8 * rp) * N + sw2((jq2 >> 2) * 32 + (jq2 & 3) + 4 * rq)] = u[rp][rq];
+      buf[row((jp2 >> 3) * 32 + (jp2 & 7) + 8 * rp) * N + sw2((jq2 >> 2) * 32 + (jq2 & 3) + 4 * rq)] = u[rp][rq];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
@@ -95,7 +98,7 @@ __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-      for (int rq = 0; rq < 4; ++rq) w3[i][rp][rq] = buf[(jp3 + 32 * rp) * N + sw2(lane + 32 * rq)];
+      for (int rq = 0; rq < 4; ++rq) w3[i][rp][rq] = buf[row(jp3 + 32 * rp) * N + sw2(lane + 32 * rq)];
     twiddle2d<4, 4, SIGN>(w3[i], tw, jp3, lane);
     dft2d<4, 4, SIGN>(w3[i]);
   }
@@ -105,8 +108,10 @@ __device__ __forceinline__ void stages_23(float2 (&v)[8][4], float2 (&w3)[2][4][
 // G(b,d) (or W0 x factors) in registers, 2D DFT (sign -1) over (c, d), natural-order slice into
 // shared memory, one TMA tensor store into the V layout.  F(c, d) = Ein(c) Ein(d) Y(c, d) m(c, d)
 // from the per-axis factors, the aperture test and the optional mask; the GSM factors G(a, c),
-// G(b, d) are read through L1.  Stage 3 reads and writes only its warp's rows, so the
-// natural-order write after it needs only a warp barrier.
+// G(b, d) are read through L1.  Stage 3 reads and writes only its warp's eight buffer rows (the
+// second exchange permutes rows by vrow), so the natural-order write after it needs only a warp
+// barrier, and each warp leaves its rows by its own TMA store (8 rows of V, 256 runs of 32 bytes),
+// which drains while the next slice is built.
 template <int SRC, bool MASK>
 __global__ void __launch_bounds__(NT, 1)
     pass_a_r128(const __grid_constant__ CUtensorMap vmap, PassAArgs p, const float2* __restrict__ Ein,
@@ -170,25 +175,25 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     dft2d<8, 4, -1>(v);
-    if (t == 0) bulk_wait_read_all();  // the previous slice's TMA store has left buf
+    if (lane == 0) bulk_wait_read_all();  // this warp's store of the previous slice has left buf
     __syncthreads();
     float2 w3[2][4][4];
-    stages_23<-1>(v, w3, buf, tw);
-    __syncwarp();  // stage 3 reads only the warp's own rows (c' = warp + 16 i + 32 rp)
+    stages_23<-1, true>(v, w3, buf, tw);
+    __syncwarp();  // stage 3 read only the warp's own buffer rows 8 warp .. 8 warp + 7
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-        for (int rq = 0; rq < 4; ++rq) buf[(warp + 16 * i + 32 * rp) * N + lane + 32 * rq] = w3[i][rp][rq];
+        for (int rq = 0; rq < 4; ++rq) buf[(8 * warp + i + 2 * rp) * N + lane + 32 * rq] = w3[i][rp][rq];
     fence_proxy_async_smem();
-    __syncthreads();
-    if (t == 0) {
-      tma_store_5d(&vmap, buf, 0, b, a, 0, 0);
+    __syncwarp();
+    if (lane == 0) {  // V rows vrow(c') = 8 warp + i + 2 rp of this slice
+      tma_store_5d(&vmap, buf + 8 * warp * N, 0, b, a, 0, 8 * warp);
       bulk_commit();
     }
   }
-  if (t == 0) bulk_wait_all();
+  if (lane == 0) bulk_wait_all();
 }
 
 constexpr size_t pass_a_smem() { return (size_t)N * N * sizeof(float2) + 2 * N * sizeof(float2); }
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(NT, 1) pass_b_r128(PassBArgs p) {
   auto prefetch = [&](int cdn) {
     if (t == 0 && cdn < N * N) {
       const int cn = cdn / N, dn = cdn % N;
-      bulk_prefetch_l2(p.V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * N * N, (unsigned)(N * N * sizeof(float2)));
+      bulk_prefetch_l2(p.V + ((size_t)(vrow<N>(cn) * (N / g) + dn / g) * g + dn % g) * N * N, (unsigned)(N * N * sizeof(float2)));
     }
   };
   prefetch(blockIdx.x + gridDim.x);

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT, 2) pass_b_r96(PassBArgs p) {
   auto prefetch = [&](int cdn) {
     if (t == 0 && cdn < N * N) {
       const int cn = cdn / N, dn = cdn % N;
-      bulk_prefetch_l2(p.V + ((size_t)(cn * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
+      bulk_prefetch_l2(p.V + ((size_t)(vrow<N>(cn) * (N / g) + dn / g) * g + dn % g) * NN, (unsigned)(NN * sizeof(float2)));
     }
   };
   prefetch(blockIdx.x);
