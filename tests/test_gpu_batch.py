@@ -242,3 +242,51 @@ def test_spectral_sum_on_common_grid():
     with pytest.raises(pw.PwError, match="no common grid"):
         pw.pw_batch_spectral_sum(b, [1.0, 1.0], I.data_ptr())
     pw.pw_batch_destroy(b)
+
+
+def test_batch_s_mu_only_pruned_pass():
+    """Instances that keep no W take the pruned second pass (two dot products per column instead of
+    the DFT over point 1): N = 128 (register-resident pass A; separable GSM behind a lens, exact by
+    the per-axis quadrature), N = 64 with aperture and mask, N = 16 in the far field, each against
+    the FP64 oracle, sequenced mode, run twice."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    cases = [  # (N, z, farfield, lam, aperture, lens, with mask, P1)
+        (128, 0.45, 0, 610e-9, 0.0, 0.35, False, (61, 66)),
+        (64, 0.3, 0, 580e-9, 0.4e-3, 0.0, True, (30, 35)),
+        (16, 0.7, 1, 633e-9, 0.0, 0.0, False, (7, 9)),
+    ]
+    insts, outs, keep = [], [], []
+    for k, (N, z, ff, lam, ap, lf, use_mask, P1) in enumerate(cases):
+        m = WL.to_c64(_mask(N, 90 + k)) if use_mask else None
+        mt = torch.from_numpy(m).cuda() if use_mask else None
+        S = torch.empty((N, N), dtype=torch.float32, device="cuda")
+        mu = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+        keep.append(mt)
+        outs.append((S, mu, m))
+        insts.append(pw.pw_instance(N, DXI, lam, z, ff, 0.1e-3, 0.05e-3, 1.0 + 0.1 * k, ap, lf,
+                                    mt.data_ptr() if use_mask else None, P1[0], P1[1], None, S.data_ptr(),
+                                    mu.data_ptr()))
+    nb = pw.pw_batch_workspace_bytes(insts, 2)
+    ws = torch.full((nb,), 0xAB, dtype=torch.uint8, device="cuda")
+    b = pw.pw_batch_create(insts, 2, ws.data_ptr(), nb, torch.cuda.current_stream().cuda_stream)
+    pw.pw_batch_set_mode(b, pw.PW_BATCH_SEQUENCED)
+    for rep in range(2):
+        for S, mu, _ in outs:
+            S.zero_()
+            mu.zero_()
+        pw.pw_batch_run(b)
+        pw.pw_batch_check(b)
+        torch.cuda.synchronize()
+        for k, ((N, z, ff, lam, ap, lf, use_mask, P1), (S, mu, m)) in enumerate(zip(cases, outs)):
+            if N == 128:
+                ref = O.gsm_separable_quadrature(N, DXI, lam, z, 0.1e-3, 0.05e-3, 1.0 + 0.1 * k, lens_f=lf)
+            else:
+                ref = _oracle(dict(N=N, z=z, ff=ff, lam=lam, ap=ap, lf=lf, mask=m, A=1.0 + 0.1 * k))
+            Sref = np.real(np.einsum("abab->ab", ref))
+            assert rel(S.cpu().numpy(), Sref) < TOL, (N, rel(S.cpu().numpy(), Sref))
+            muref = O.degree_of_coherence(ref, *P1)
+            sel = Sref >= 1e-4 * Sref.max()
+            assert rel(mu.cpu().numpy()[sel], muref[sel]) < TOL, (N, rel(mu.cpu().numpy()[sel], muref[sel]))
+            del ref
+    pw.pw_batch_destroy(b)
