@@ -32,7 +32,8 @@ __all__ = [
     "apply_mask", "centred_dft2", "propagate_fft", "propagate_direct", "propagate_rows",
     "propagate_adjoint", "spectral_density", "degree_of_coherence", "gsm_closed_form",
     "gsm_separable_quadrature", "propagation_scale", "gsm_beam_parameters", "propagate_rows_blocks",
-    "propagate_rows_gsm", "s_loss", "s_loss_gradient", "propagate_padded", "padded_dft_matrix",
+    "propagate_rows_gsm", "propagate_rows_diagonal", "s_loss", "s_loss_gradient", "propagate_padded",
+    "padded_dft_matrix",
     "propagate_rows_gsm_padded", "axis_kernels", "bilinear_probes", "bilinear_probes_gsm",
     "sm_loss", "adjoint_source", "sm_loss_gradient",
 ]
@@ -217,6 +218,28 @@ def propagate_rows(source_slice, N, dxi, lam, z, rows, farfield=False):
         for j1 in range(N):
             inner += c[:, i1, j1, None, None] * source_slice(i1, j1)[None]
     inner *= qin[None]
+    out = centred_dft2(inner, axes=(1, 2), sign=-1)
+    qout = q(z, _r2_grid(N, dx), lam)
+    for r, (a, b) in enumerate(rows):
+        out[r] *= propagation_scale(dxi, lam, z) * np.conj(qout[a, b]) * qout
+    return out
+
+
+def propagate_rows_diagonal(d, w, N, dxi, lam, z, rows, farfield=False):
+    """Rows of the propagated CSDA of the delta-correlated source W0(xi1, xi2) = w d(xi1) when
+    xi1 = xi2 and 0 otherwise (Sec. 2.3's incoherent limit on the grid): in the point-1 sum of
+    propagate_rows only xi1 = xi2 survives, so
+      inner(X1, xi2) = q*(xi2) exp(+2 pi i X1.xi2/(lambda z)) w d(xi2)
+    and the point-2 sum is the same centred DFT.  d is N x N (real), rows a list of (i1', j1')."""
+    x, y = axis_coords(N, dxi)
+    dx = output_sampling(N, dxi, lam, z)
+    X, Y = axis_coords(N, dx)
+    rows = list(rows)
+    qin = np.ones((N, N), dtype=np.complex128) if farfield else q(z, _r2_grid(N, dxi), lam)
+    inner = np.empty((len(rows), N, N), dtype=np.complex128)
+    for r, (a, b) in enumerate(rows):
+        ph = (X[a] * x[:, None] + Y[b] * y[None, :]) / (lam * z)
+        inner[r] = np.conj(qin) * np.exp(2j * np.pi * ph) * (w * np.asarray(d, dtype=np.float64)) * qin
     out = centred_dft2(inner, axes=(1, 2), sign=-1)
     qout = q(z, _r2_grid(N, dx), lam)
     for r, (a, b) in enumerate(rows):

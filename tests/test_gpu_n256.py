@@ -2,8 +2,8 @@
 unit-modulus screen with 3 px correlation) against the oracle: 65 output rows spread over the grid
 (edges included) from the row route of Eq. W_fresnel, 16 random bilinear probes u^H W_B v over the
 whole array from W0 through the kernel sums of Eq. W_general, S and mu at the rows' points, plus
-Hermiticity, power and trace conservation (GPU); a non-Hermitian uploaded array on the four
-streaming passes; and the
+Hermiticity, power and trace conservation (GPU); a non-Hermitian uploaded array and a
+delta-correlated source in the far field on the three-pass engine; and the
 same workload with the first radix-16 stage on the tensor cores (split-BF16x3), whose FP64
 errors for W, S and mu are printed next to those of the FP32 path."""
 import numpy as np
@@ -287,3 +287,28 @@ def test_n256_adjoint_dot_product_identity():
     e = abs(left - right) / abs(right)
     record("n256_adjoint_dot", left=left, right=right, rel=e)
     assert e < 1e-5, (left, right, e)
+
+
+def test_n256_diagonal_far_field():
+    """Delta-correlated source W0 = w d(xi1) delta(xi1 - xi2) generated in-kernel, far field z = 2 m:
+    12 output rows (corners and edges included) against the oracle's collapsed row sum, and the
+    whole S against its closed form S(X) = s w sum_xi d(xi) (the phases cancel on the diagonal)."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    N, dxi, lam, z, w = 256, 20e-6, 633e-9, 2.0, 0.5
+    d = (0.2 + WL.uniform01(31, N * N).reshape(N, N)).astype(np.float32)
+    c = pw.CSD(N, dxi, lam)
+    dd = torch.from_numpy(d).cuda()
+    pw.pw_source_diagonal(c.h, dd.data_ptr(), w)
+    c.propagate_farfield(z)
+    S = c.spectral_density().cpu().numpy().astype(np.float64)
+    rows = [(0, 0), (0, 255), (255, 0), (255, 255), (128, 128), (1, 64), (64, 200), (127, 129), (200, 37),
+            (250, 3), (90, 140), (160, 160)]
+    Wrows = [c.W[a, b].cpu().numpy().astype(np.complex128) for a, b in rows]
+    pw.pw_csd_check(c.h)
+    c.close()
+    ref = O.propagate_rows_diagonal(d.astype(np.float64), w, N, dxi, lam, z, rows, farfield=True)
+    errs = [np.linalg.norm(Wrows[r] - ref[r]) / np.linalg.norm(ref[r]) for r in range(len(rows))]
+    assert max(errs) < 1e-5, errs
+    S_ref = O.propagation_scale(dxi, lam, z) * w * d.astype(np.float64).sum()
+    assert np.linalg.norm(S - S_ref) / (S_ref * N) < 1e-5

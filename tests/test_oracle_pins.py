@@ -533,3 +533,28 @@ def test_adjoint_source_reduces_to_s_loss():
     D = np.zeros_like(Y)
     D[i[:, None], i[None, :], i[:, None], i[None, :]] = 0.5 * gS
     assert np.abs(Y - D).max() == 0
+
+
+@pytest.mark.parametrize("farfield", [False, True])
+def test_diagonal_rows_match_general_rows(farfield):
+    """propagate_rows_diagonal (the delta-correlated source's collapsed point-1 sum) against
+    propagate_rows on the same source written out slice by slice, and against the FFT route."""
+    N = 12
+    d = 0.3 + WL.uniform01(5, N * N).reshape(N, N)
+    w = 0.7
+    rows = [(0, 0), (5, 7), (11, 3)]
+
+    def slice_fn(i, j):
+        s = np.zeros((N, N), dtype=np.complex128)
+        s[i, j] = w * d[i, j]
+        return s
+    got = O.propagate_rows_diagonal(d, w, N, DXI, LAM, 0.4, rows, farfield=farfield)
+    ref = O.propagate_rows(slice_fn, N, DXI, LAM, 0.4, rows, farfield=farfield)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    W0 = np.zeros((N,) * 4, dtype=np.complex128)
+    for i in range(N):
+        for j in range(N):
+            W0[i, j, i, j] = w * d[i, j]
+    full, _ = O.propagate_fft(W0, DXI, LAM, 0.4, farfield=farfield)
+    for r, (a, b) in enumerate(rows):
+        assert np.abs(got[r] - full[a, b]).max() <= 1e-12 * np.abs(full).max()
