@@ -131,8 +131,8 @@ pw_status pw_source_mask(pw_csd* h, const pw_c32* dev_mask);
  * previous run or built by the user).  dev_W0 (N^4 complex64, device) may be dev_W itself.
  * hermitian != 0 declares W0(xi2, xi1) = conj W0(xi1, xi2) (true of every CSD, Sec. 3.3), which
  * lets the second pass store its output rows contiguously; hermitian == 0 selects the
- * general (strided-store) second pass for N <= 128, the four streaming passes at N = 256, and the
- * dense path needs no declaration.  Read during the next propagation. */
+ * general (strided-store) second pass for N <= 128.  The three-pass engine at N = 256 and the
+ * dense path never use Hermiticity and need no declaration.  Read during the next propagation. */
 pw_status pw_source_array(pw_csd* h, const pw_c32* dev_W0, int hermitian);
 
 /* Delta-correlated (spatially incoherent) source W0 = weight d(xi1) delta(xi1 - xi2) with real
@@ -282,7 +282,10 @@ pw_status pw_csd_pass_times3(pw_csd* h, double* ms_first, double* ms_second, dou
  *     (instance, pass, slice chunk) items; pass-B work of an instance starts after its pass-A
  *     work (bounded waits, see pw_batch_check);
  *   PW_BATCH_SEQUENCED: the instances one after the other on the single-instance kernels (each
- *     fills the GPU), with pass B storing S, the mu numerator and W only when dev_W is given.
+ *     fills the GPU): pass A, then pass B with S, the mu numerator and W when dev_W is given;
+ *     without dev_W the second pass computes only the two outputs per column that S and the mu
+ *     numerator use (dot products over the point-1 pair, Eq. W_fresnel's point-1 sum at X1 = X2
+ *     and at X1 = P1), reading the half-transformed CSDA in its own layout.
  * The default is SEQUENCED when every instance has N >= 64, else PERSISTENT.  In both modes the
  * half-transformed CSDAs share a pool of `pool` buffers of the largest N (instance i uses slot
  * i mod pool).  pw_batch_run enqueues only device work (no allocation, no synchronisation), so
