@@ -227,4 +227,69 @@ __global__ void w0_gradient_kernel(float2* R, int N, float twoc, const float2* _
   }
 }
 
+
+// ---- pass A of an adjoint propagation written directly (N <= 128) ------------------------------
+// The adjoint source (AdjSlice) of slice x1 = (a, b) is d(x1) at x2 = x1, plus, for the Hermitian
+// part of a mu term, conj(r(x1)) / 2 at x2 = P1, plus the row w_r r(x2) in the slice x1 = P1.  The
+// sign -1 2D DFT of pass A maps a point to a plane wave, so with s_ab = A conj F(a, b):
+//   V(a, b; c', d') = s_ab [ d(x1) F(a, b) e^{-2 pi i (a c' + b d')/N}
+//                            + col(x1) F(P1) e^{-2 pi i (iP c' + jP d')/N} ]
+//                     + [x1 = P1] s_P1 w_r sum_{c,d} e^{-2 pi i (c c' + d d')/N} F(c, d) r(c, d).
+// adj_row_kernel writes the last term (one 2D DFT, separable: N blocks over c', N threads over d)
+// into the P1 slice's own places of V; adj_direct_kernel then writes every element of V in memory
+// order (coalesced), adding to those.  Same values as the transform of the same source, in
+// exact arithmetic; this replaces pass A's 2D DFT of an almost empty source by one V write.
+template <int N>
+__global__ void __launch_bounds__(N) adj_row_kernel(PassAArgs p, float2* __restrict__ V) {
+  __shared__ float2 u[N];
+  __shared__ float2 tw[N];
+  const int cq = blockIdx.x, t = threadIdx.x, p1 = p.iP * N + p.jP;
+  tw[t] = p.tw[t];
+  __syncthreads();
+  float2 acc = make_float2(0.f, 0.f);  // sum_c e^{-2 pi i c c' / N} F(c, d) r(c, d), d = t
+  for (int c = 0; c < N; ++c)
+    acc = cadd(acc, cmul(tw[(c * cq) % N], cmul(__ldg(p.F + c * N + t), __ldg(p.cross + c * N + t))));
+  u[t] = acc;
+  __syncthreads();
+  float2 r = make_float2(0.f, 0.f);  // d' = t
+  for (int d = 0; d < N; ++d) r = cadd(r, cmul(tw[(d * t) % N], u[d]));
+  const float2 coef = cscale(cconj(__ldg(p.F + p1)), p.A * (p.herm ? 0.5f : 1.f));
+  V[v_offset<N>(p1, cq, t)] = cmul(coef, r);
+}
+
+template <int N> __host__ __device__ constexpr int adj_nt() { return 4 * N < 512 ? 4 * N : 512; }
+
+template <int N>
+__global__ void __launch_bounds__(adj_nt<N>()) adj_direct_kernel(PassAArgs p, float2* __restrict__ V) {
+  constexpr int G = vgroup<N>(), ROW = N * G, NT = adj_nt<N>(), SLOTS = ROW / NT;
+  static_assert(G == 4 && ROW % NT == 0, "rows of V split evenly over the block");
+  __shared__ float2 tw[N];
+  const int t = threadIdx.x;
+  for (int i = t; i < N; i += NT) tw[i] = p.tw[i];
+  __syncthreads();
+  const int p1 = p.iP * N + p.jP;
+  const bool rowterm = p.cross != nullptr;         // the P1 slice holds adj_row_kernel's term
+  const bool colterm = p.cross != nullptr && p.herm;
+  const float2 fp1 = __ldg(p.F + p1);
+  constexpr int ROWS = N * (N / G) * N;            // V rows (vrow(c'), d'/G, a) of N G values
+  for (int rr = blockIdx.x; rr < ROWS; rr += gridDim.x) {
+    const int a = rr % N, t2 = rr / N, dg = t2 % (N / G), cq = vrow_inv<N>(t2 / (N / G));
+    const int ac = (a * cq) % N, pc = (p.iP * cq) % N;
+    float2* Vr = V + (size_t)rr * ROW;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int k = t + NT * s, b = k / G, dq = G * dg + k % G, ab = a * N + b;
+      const float2 fab = __ldg(p.F + ab);
+      const float dd = p.diag ? __ldg(p.diag + ab) : 0.f;
+      float2 v = cscale(tw[(ac + b * dq) % N], p.A * dd * (fab.x * fab.x + fab.y * fab.y));
+      if (colterm) {
+        const float2 col = cscale(cconj(__ldg(p.cross + ab)), 0.5f * p.A);
+        v = cadd(v, cmul(cmul(cconj(fab), col), cmul(fp1, tw[(pc + p.jP * dq) % N])));
+      }
+      if (rowterm && ab == p1) v = cadd(v, Vr[k]);
+      Vr[k] = v;
+    }
+  }
+}
+
 }  // namespace pw

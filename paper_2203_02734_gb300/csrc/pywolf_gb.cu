@@ -355,6 +355,27 @@ cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const
   }
 }
 
+// Pass A of an adjoint propagation: at N <= 128 (V layout with runs of 4) V is written directly
+// from the almost empty adjoint source (grad.cuh: adj_row_kernel for the P1 row when a mu term is
+// present, then adj_direct_kernel); elsewhere the engine's pass A with the SRC_ADJ source.
+template <int N>
+cudaError_t launch_a_adjoint(const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                             const R128Extra& x, cudaStream_t s) {
+  if constexpr (N >= 16 && N <= 128 && pw::vgroup<N>() == 4) {
+    float2* V = const_cast<float2*>(b.V);
+    if (a.cross) {
+      pw::adj_row_kernel<N><<<N, N, 0, s>>>(a, V);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    constexpr int nt = pw::adj_nt<N>(), rows = N * (N / 4) * N;
+    pw::adj_direct_kernel<N><<<std::min(rows, num_sms() * (2048 / nt)), nt, 0, s>>>(a, V);
+    return cudaGetLastError();
+  } else {
+    return launch_a_mode<N, pw::SRC_ADJ>(vmap, a, x, s);
+  }
+}
+
 // ev: nullptr or three events recorded before pass A, between the passes and after pass B.
 // grad: pass B reduces the GSM parameter gradients of an adjoint propagation (W_GRAD) instead of
 // storing W.
@@ -365,7 +386,7 @@ cudaError_t launch_passes(int src, bool herm, bool grad, const CUtensorMap& vmap
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
   if (src == pw::SRC_GSM) e = launch_a_mode<N, pw::SRC_GSM>(vmap, a, x, s);
   else if (src == pw::SRC_DIAG) e = launch_a_mode<N, pw::SRC_DIAG>(vmap, a, x, s);
-  else if (src == pw::SRC_ADJ) e = launch_a_mode<N, pw::SRC_ADJ>(vmap, a, x, s);
+  else if (src == pw::SRC_ADJ) e = launch_a_adjoint<N>(vmap, a, b, x, s);
   else e = launch_a_mode<N, pw::SRC_ARRAY>(vmap, a, x, s);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
