@@ -355,13 +355,15 @@ cudaError_t launch_a_mode(const CUtensorMap& vmap, const pw::PassAArgs& a, const
   }
 }
 
-// Pass A of an adjoint propagation: at N <= 128 (V layout with runs of 4) V is written directly
-// from the almost empty adjoint source (grad.cuh: adj_row_kernel for the P1 row when a mu term is
-// present, then adj_direct_kernel); elsewhere the engine's pass A with the SRC_ADJ source.
-template <int N>
-cudaError_t launch_a_adjoint(const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
-                             const R128Extra& x, cudaStream_t s) {
+// Pass A of a source with at most one or two points per slice: the adjoint source (SRC_ADJ) and
+// the delta-correlated source (SRC_DIAG, the adjoint form's diagonal term with the source's d and
+// weight).  At N <= 128 (V layout with runs of 4) V is written directly (grad.cuh: adj_row_kernel
+// for the P1 row of a mu term, then adj_direct_kernel); elsewhere the engine's pass A.
+template <int N, int SRC>
+cudaError_t launch_a_sparse(const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
+                            const R128Extra& x, cudaStream_t s) {
   if constexpr (N >= 16 && N <= 128 && pw::vgroup<N>() == 4) {
+    if (SRC == pw::SRC_DIAG && a.cross) return cudaErrorInvalidValue;  // a diagonal source has no row
     float2* V = const_cast<float2*>(b.V);
     if (a.cross) {
       pw::adj_row_kernel<N><<<N, N, 0, s>>>(a, V);
@@ -372,7 +374,7 @@ cudaError_t launch_a_adjoint(const CUtensorMap& vmap, const pw::PassAArgs& a, co
     pw::adj_direct_kernel<N><<<std::min(rows, num_sms() * (2048 / nt)), nt, 0, s>>>(a, V);
     return cudaGetLastError();
   } else {
-    return launch_a_mode<N, pw::SRC_ADJ>(vmap, a, x, s);
+    return launch_a_mode<N, SRC>(vmap, a, x, s);
   }
 }
 
@@ -385,8 +387,8 @@ cudaError_t launch_passes(int src, bool herm, bool grad, const CUtensorMap& vmap
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
   if (src == pw::SRC_GSM) e = launch_a_mode<N, pw::SRC_GSM>(vmap, a, x, s);
-  else if (src == pw::SRC_DIAG) e = launch_a_mode<N, pw::SRC_DIAG>(vmap, a, x, s);
-  else if (src == pw::SRC_ADJ) e = launch_a_adjoint<N>(vmap, a, b, x, s);
+  else if (src == pw::SRC_DIAG) e = launch_a_sparse<N, pw::SRC_DIAG>(vmap, a, b, x, s);
+  else if (src == pw::SRC_ADJ) e = launch_a_sparse<N, pw::SRC_ADJ>(vmap, a, b, x, s);
   else e = launch_a_mode<N, pw::SRC_ARRAY>(vmap, a, x, s);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
