@@ -77,6 +77,70 @@ template <int SIGN> __device__ __forceinline__ float2 twid(const float2* tw, int
 // the next tile's first exchange waits (per warp, before the block barrier) until those stores have
 // read the buffer.  The twiddle e^{-2 pi i r k_l / 256} is applied by pass 2, which has issue slots
 // to spare.
+// Pass 1's codelets with each complex add / subtract as one packed FP32x2 instruction (the same
+// rounding as two FP32 adds, so the same results as Dft<R, S>): fewer issued instructions where
+// pass 1 is bound by its arithmetic.  Passes 2 and 3 keep Dft (packed adds slowed pass 2).
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 up2(unsigned long long r) {
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(r));
+  return d;
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return up2(d);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return up2(d);
+}
+template <int R, int S> struct PDft;
+template <int S> struct PDft<4, S> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t0 = padd(v[0], v[2]), t1 = psub(v[0], v[2]);
+    const float2 t2 = padd(v[1], v[3]), t3 = mul_si<S>(psub(v[1], v[3]));
+    v[0] = padd(t0, t2);
+    v[2] = psub(t0, t2);
+    v[1] = padd(t1, t3);
+    v[3] = psub(t1, t3);
+  }
+};
+template <int S> struct PDft<8, S> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    PDft<4, S>::run(e);
+    PDft<4, S>::run(o);
+    o[1] = mul_cs<S>(o[1], kR2, kR2);
+    o[2] = mul_si<S>(o[2]);
+    o[3] = mul_cs<S>(o[3], -kR2, kR2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = padd(e[k], o[k]);
+      v[k + 4] = psub(e[k], o[k]);
+    }
+  }
+};
+template <int RP, int RQ, int S> __device__ __forceinline__ void pdft2d(float2 (&v)[RP][RQ]) {
+#pragma unroll
+  for (int rq = 0; rq < RQ; ++rq) {
+    float2 c[RP];
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) c[rp] = v[rp][rq];
+    PDft<RP, S>::run(c);
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) v[rp][rq] = c[rp];
+  }
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) PDft<RQ, S>::run(v[rp]);
+}
+
 // Position of k_l along the k_l index of Y: the four rows k_l = w + 16 i that stage 3 of warp w
 // owns are adjacent (4 w + i), so that one TMA store moves them.
 __device__ __forceinline__ int kperm(int kl) { return 4 * (kl & 15) + (kl >> 4); }
@@ -127,13 +191,13 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(const __grid_constant__ C
       }
     }
 #pragma unroll
-    for (int rp = 0; rp < 4; ++rp) Dft<8, -1>::run(v[rp]);  // rows first: the first rows' DFTs overlap later loads
+    for (int rp = 0; rp < 4; ++rp) PDft<8, -1>::run(v[rp]);  // rows first: the first rows' DFTs overlap later loads
 #pragma unroll
     for (int rq = 0; rq < 8; ++rq) {
       float2 cc[4];
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp) cc[rp] = v[rp][rq];
-      Dft<4, -1>::run(cc);
+      PDft<4, -1>::run(cc);
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp) v[rp][rq] = cc[rp];
     }
@@ -149,7 +213,7 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(const __grid_constant__ C
 #pragma unroll
       for (int rq = 0; rq < 8; ++rq) v[rp][rq] = buf[(w + 16 * rp) * N + xs1(lane + 32 * rq)];
     r128::twiddle2d<4, 8, -1>(v, tw, 16 * (w & 3), 4 * (lane & 7));
-    r128::dft2d<4, 8, -1>(v);
+    pdft2d<4, 8, -1>(v);
     __syncthreads();
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp)
@@ -172,7 +236,7 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(const __grid_constant__ C
     for (int h = 0; h < 2; ++h) {
       const int jq = lane + 32 * h;
       r128::twiddle2d<4, 4, -1>(u[h], tw, 4 * w, jq);
-      r128::dft2d<4, 4, -1>(u[h]);
+      pdft2d<4, 4, -1>(u[h]);
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
