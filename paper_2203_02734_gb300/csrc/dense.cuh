@@ -97,6 +97,13 @@ struct AxisArgs {
   float* S;
   int stall;  // failure-detection test (0 = off): CTA 0 of the tensor-core kernel never copies operand chunk
               // `stall` (> 0), or never announces A tile -stall (< 0)
+  // Tensor-core kernel, first contraction (L = 1) of a GSM source: gen != 0 builds the input
+  // W0(a, b, c, d) = A conj(M0(a, b)) G(a, c) G(b, d) M0(c, d) in the converters instead of reading
+  // `in` (source_kernel is then not run).
+  int gen;
+  const float* G;
+  const float2* M0;
+  float A;
 };
 
 constexpr int BM = 64, BN = 64, BK = 16, PITCH = 66, NT = 256;

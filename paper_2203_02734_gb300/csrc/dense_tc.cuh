@@ -141,6 +141,16 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
   const long long L = p.L, ncols = p.ncols;
   const long long j = (long long)blockIdx.x * 128 + m;
   const long long jb = (t < 256 && j < ncols) ? dense::col_base(j, L, N) : -1;
+  // gen (L = 1, column j = (a N + b) N + c): W0(a, b, c, n) = [A conj M0(a, b) G(a, c)] M0(c, n) G(b, n)
+  float2 gcol = make_float2(0.f, 0.f);
+  const float2* gm = nullptr;
+  const float* gg = nullptr;
+  if (p.gen && jb >= 0) {
+    const int c = (int)(j % N), b = (int)((j / N) % N), a = (int)(j / ((long long)N * N));
+    gcol = cscale(cconj(__ldg(p.M0 + a * N + b)), p.A * __ldg(p.G + a * N + c));
+    gm = p.M0 + c * N;
+    gg = p.G + b * N;
+  }
 
   if (w == 0) tc16::tmem_alloc(tslot, tmem_cols(N));
   if (t == 0) {
@@ -224,7 +234,8 @@ __global__ void __launch_bounds__(NT, 1) axis_tc_kernel(dense::AxisArgs p, const
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int n = 16 * c + 8 * ks + i;
-        x[i] = (jb >= 0 && n < N) ? p.in[jb + (long long)n * L] : make_float2(0.f, 0.f);
+        x[i] = (jb >= 0 && n < N) ? (gm ? cscale(cmul(gcol, __ldg(gm + n)), __ldg(gg + n)) : p.in[jb + (long long)n * L])
+                                  : make_float2(0.f, 0.f);
       }
       if (c >= ABUF) {  // A tile c mod ABUF last held chunk c - ABUF
         const int pc = c - ABUF;

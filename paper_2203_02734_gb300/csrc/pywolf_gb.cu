@@ -521,9 +521,9 @@ pw_status build_tables(pw_csd* h, double z, bool farfield) {
 bool has_masks(const pw_csd* h) { return h->aperture > 0.0 || h->lens_f != 0.0 || h->mask != nullptr; }
 
 // Zero padding (Nz > N) or a grid size without an FFT plan: four dense axis contractions
-// (dense.cuh).  W0 is built in W, then d (W -> work), c (work -> W), b (W -> work) and
-// a (work -> W, with the scale and S).  Events as for the FFT passes: the first two
-// contractions count as the first pass.
+// (dense.cuh).  W0 is built in W (for a GSM source on the tensor cores, inside the first
+// contraction instead), then d (W -> work), c (work -> W), b (W -> work) and a (work -> W, with the
+// scale and S).  Events as for the FFT passes: the first two contractions count as the first pass.
 pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   const int N = h->N, Nz = h->Nz > 0 ? h->Nz : N;
   pw_status st = build_tables(h, z, farfield);  // G and M0 (the FFT factors are not used here)
@@ -550,8 +550,13 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   sa.diag = h->diag;
   sa.A = (float)h->A;
   sa.W = reinterpret_cast<float2*>(h->W);
-  pw::dense::source_kernel<<<num_sms() * 8, 256, 0, h->stream>>>(sa);
+  const bool tc = h->dft_mode != PW_DFT_FP32 && N <= pw::dense_tc::MAX_N;
+  const bool gen = tc && sa.mode == pw::SRC_GSM;  // the first tensor-core contraction builds W0 itself
+  if (!gen) pw::dense::source_kernel<<<num_sms() * 8, 256, 0, h->stream>>>(sa);
   pw::dense::AxisArgs ax{};
+  ax.G = h->G;
+  ax.M0 = h->M0;
+  ax.A = (float)h->A;
   ax.N = N;
   ax.ncols = (long long)N * N * N;
   ax.E = h->F;
@@ -560,7 +565,6 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
   float2* Wf = reinterpret_cast<float2*>(h->W);
   float2* Xf = reinterpret_cast<float2*>(h->work);
   const long long L[4] = {1, N, (long long)N * N, (long long)N * N * N};
-  const bool tc = h->dft_mode != PW_DFT_FP32 && N <= pw::dense_tc::MAX_N;
   if (tc) {  // the split matrices of E (point 2) and conj(E) (point 1), then four tensor-core passes
     const size_t qb = (size_t)pw::dense_tc::nchunks(N) * pw::dense_tc::chunk_bytes(N);
     if (!h->qbuf && (e = cudaMalloc(&h->qbuf, 2 * qb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc of the split DFT matrices");
@@ -594,6 +598,7 @@ pw_status propagate_dense(pw_csd* h, double z, bool farfield, bool herm) {
       ax.scale = pass == 3 ? (float)((d * d / lz) * (d * d / lz)) : 1.0f;
       const unsigned char* qm = q + (pass < 2 ? 0 : qb);
       if (pass > 0) ax.stall = 0;
+      ax.gen = gen && pass == 0 ? 1 : 0;
       if (abuf == 2) {
         if (pass < 3)
           pw::dense_tc::axis_tc_kernel<false, 2><<<tgrid, pw::dense_tc::NT, smem, h->stream>>>(ax, qm, h->err);
