@@ -194,3 +194,65 @@ def test_adjoint_entry_point_rejects_bad_arguments():
     pw.pw_csd_set_padding(c.h, 24)
     assert "PW_EUNSUPPORTED" in call(dev_dS=dS.data_ptr(), dev_grad3=g3.data_ptr())
     c.close()
+
+
+@pytest.mark.parametrize("N,farfield", [(64, False), (128, False), (128, True)])
+def test_adjoint_dot_product_identity_direct_pass_a(N, farfield):
+    """The adjoint call at N = 64 and 128, whose first pass writes V directly from the sparse
+    adjoint source (plane waves per slice plus the transformed P1 row): for the linear loss
+    L(W_B) = Re <2 Y, W_B> with Y the adjoint source of (dL/dS, dL/dmu) (reading R22), the
+    gradient in a general W0 is 2 P^H(Y), so Re <dL/dW0, W0> equals Re <2 Y, P(W0)>: the left side
+    from the N^4 gradient the call writes, the right side from S and the P1 row of the forward
+    (FP64 sums on both sides).  W0 = GSM x phase screen."""
+    import torch
+    import paper_2203_02734_gb300 as pw
+    dxi, lam, z, sS, sM, A = 20e-6, 633e-9, 0.5, 0.1e-3, 0.05e-3, 1.3
+    P1 = (N // 2 - 3, N // 2 + 2)
+    mask = WL.to_c64(WL.phase_screen(N, seed=WL.SEED + 11, corr_px=3.0))
+    c = pw.CSD(N, dxi, lam)
+    mt = torch.from_numpy(mask).cuda()
+    c.source_gsm(sS, sM, A)
+    c.source_mask(mt)
+    (c.propagate_farfield if farfield else c.propagate_fresnel)(z)
+    S = c.spectral_density()
+    mu = c.degree_of_coherence(*P1)
+    row = c.W[P1[0], P1[1]].clone()
+    torch.cuda.synchronize()
+    Sh0 = S.cpu().numpy().astype(np.float64)
+    gS_h = 0.5 + 0.5 * WL.uniform01(81, N * N).reshape(N, N)
+    u = WL.uniform01(82, 2 * N * N).reshape(2, N, N) - 0.5
+    region = Sh0 >= 1e-4 * Sh0.max()
+    scale = 0.01 * np.sum(gS_h * Sh0) / max(float(np.sum(np.abs(mu.cpu().numpy())[region])), 1e-30)
+    gS = torch.tensor(gS_h, dtype=torch.float32, device="cuda")
+    gmu = torch.tensor(np.where(region, scale * (u[0] + 1j * u[1]), 0.0), dtype=torch.complex64, device="cuda")
+    adj = pw.pw_adjoint()
+    adj.dev_dS, adj.dev_dmu, adj.iP, adj.jP = gS.data_ptr(), gmu.data_ptr(), P1[0], P1[1]
+    adj.dev_S, adj.dev_mu, adj.grad_W0 = S.data_ptr(), mu.data_ptr(), 1
+    (pw.pw_propagate_farfield_adjoint if farfield else pw.pw_propagate_fresnel_adjoint)(c.h, z, adj)
+    pw.pw_csd_check(c.h)
+    x, _ = O.axis_coords(N, dxi)
+    gax = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (4 * sS ** 2) - (x[:, None] - x[None, :]) ** 2 / (2 * sM ** 2))
+    gt = torch.tensor(gax, dtype=torch.float64, device="cuda")
+    m64 = torch.tensor(mask.astype(np.complex128), device="cuda")
+    left = 0.0
+    for a in range(N):  # W0[a, b, c, d] = A conj(m[a, b]) g[a, c] g[b, d] m[c, d]
+        blk = (A * torch.conj(m64[a])[:, None, None] * gt[a][None, :, None] * gt[:, None, :]) * m64[None]
+        left += float(torch.sum(torch.conj(c.W[a].cdouble()) * blk).real)
+    c.close()
+    Sh = S.cpu().numpy().astype(np.float64)
+    muh = mu.cpu().numpy().astype(np.complex128)
+    rowh = row.cpu().numpy().astype(np.complex128)
+    gSh = gS.cpu().numpy().astype(np.float64)
+    gmuh = gmu.cpu().numpy().astype(np.complex128)
+    sp = Sh[P1]
+    ok = sp * Sh > 0
+    D = np.sqrt(np.where(ok, sp * Sh, 1.0))
+    r = np.where(ok, np.real(np.conj(gmuh) * muh), 0.0)
+    dS = gSh - np.where(ok & (Sh > 0), r / (2 * np.where(Sh > 0, Sh, 1.0)), 0.0)
+    dS[P1] -= r.sum() / (2 * sp)
+    gw = np.where(ok, gmuh / D, 0.0)
+    right = float(np.sum(dS * Sh) + np.real(np.sum(np.conj(gw) * rowh)))
+    e = abs(left - right) / abs(right)
+    from gpu_cases import record
+    record("adjoint_dot_n%d%s" % (N, "_ff" if farfield else ""), left=left, right=right, rel=e)
+    assert e < 1e-5, (left, right, e)
