@@ -261,7 +261,7 @@ template <int N> __host__ __device__ constexpr int adj_nt() { return 4 * N < 512
 
 template <int N>
 __global__ void __launch_bounds__(adj_nt<N>()) adj_direct_kernel(PassAArgs p, float2* __restrict__ V) {
-  constexpr int G = vgroup<N>(), ROW = N * G, NT = adj_nt<N>(), SLOTS = ROW / NT;
+  constexpr int G = vgroup<N>(), ROW = N * G, NT = adj_nt<N>(), SLOTS = ROW / NT, NG = N / G;
   static_assert(G == 4 && ROW % NT == 0, "rows of V split evenly over the block");
   __shared__ float2 tw[N];
   const int t = threadIdx.x;
@@ -271,23 +271,59 @@ __global__ void __launch_bounds__(adj_nt<N>()) adj_direct_kernel(PassAArgs p, fl
   const bool rowterm = p.cross != nullptr;         // the P1 slice holds adj_row_kernel's term
   const bool colterm = p.cross != nullptr && p.herm;
   const float2 fp1 = __ldg(p.F + p1);
-  constexpr int ROWS = N * (N / G) * N;            // V rows (vrow(c'), d'/G, a) of N G values
-  for (int rr = blockIdx.x; rr < ROWS; rr += gridDim.x) {
-    const int a = rr % N, t2 = rr / N, dg = t2 % (N / G), cq = vrow_inv<N>(t2 / (N / G));
-    const int ac = (a * cq) % N, pc = (p.iP * cq) % N;
+  // V rows (vrow(c'), d'/G, a) of N G values; block blockIdx.x takes a contiguous range of rows, so
+  // that a runs fastest: b d' mod N is fixed for N rows and a c' mod N grows by c' per row.
+  constexpr int ROWS = N * NG * N;
+  const int per = (ROWS + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * per, r1 = min(ROWS, r0 + per);
+  if (r0 >= r1) return;
+  int a = r0 % N, dg = (r0 / N) % NG, cr = r0 / (N * NG);
+  int cq = vrow_inv<N>(cr), ac = (a * cq) % N;
+  int bdq[SLOTS], jdq[SLOTS];  // b d' mod N and jP d' mod N of the thread's values in the current (c', d'/G)
+  auto set_d = [&]() {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int k = t + NT * s, dq = G * dg + (k % G);
+      bdq[s] = ((k / G) * dq) % N;
+      jdq[s] = (p.jP * dq) % N;
+    }
+  };
+  set_d();
+  int pc = (p.iP * cq) % N;
+  for (int rr = r0; rr < r1; ++rr) {
     float2* Vr = V + (size_t)rr * ROW;
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
-      const int k = t + NT * s, b = k / G, dq = G * dg + k % G, ab = a * N + b;
+      const int k = t + NT * s, ab = a * N + k / G;
       const float2 fab = __ldg(p.F + ab);
       const float dd = p.diag ? __ldg(p.diag + ab) : 0.f;
-      float2 v = cscale(tw[(ac + b * dq) % N], p.A * dd * (fab.x * fab.x + fab.y * fab.y));
+      int i1 = ac + bdq[s];
+      i1 -= i1 >= N ? N : 0;
+      float2 v = cscale(tw[i1], p.A * dd * (fab.x * fab.x + fab.y * fab.y));
       if (colterm) {
+        int i2 = pc + jdq[s];
+        i2 -= i2 >= N ? N : 0;
         const float2 col = cscale(cconj(__ldg(p.cross + ab)), 0.5f * p.A);
-        v = cadd(v, cmul(cmul(cconj(fab), col), cmul(fp1, tw[(pc + p.jP * dq) % N])));
+        v = cadd(v, cmul(cmul(cconj(fab), col), cmul(fp1, tw[i2])));
       }
       if (rowterm && ab == p1) v = cadd(v, Vr[k]);
       Vr[k] = v;
+    }
+    // next row: a + 1, then d'/G + 1, then c'
+    ac += cq;
+    ac -= ac >= N ? N : 0;
+    if (++a == N) {
+      a = 0;
+      ac = 0;
+      if (++dg == NG) {
+        dg = 0;
+        ++cr;
+        if (cr < N) {
+          cq = vrow_inv<N>(cr);
+          pc = (p.iP * cq) % N;
+        }
+      }
+      set_d();
     }
   }
 }
