@@ -521,7 +521,7 @@ static __global__ void s_mu_kernel(SMuArgs a) {
 template <int N> __host__ __device__ constexpr int smu_nt() { return 4 * N < 512 ? 4 * N : 512; }
 
 template <int N>
-__global__ void __launch_bounds__(smu_nt<N>()) smu_from_v_kernel(PassBArgs p) {
+__global__ void __launch_bounds__(smu_nt<N>(), 2048 / smu_nt<N>()) smu_from_v_kernel(PassBArgs p) {
   constexpr int G = 4, ROW = N * G, NT = smu_nt<N>(), SLOTS = ROW / NT, NW = NT / 32, NG = N * N / G;
   static_assert(ROW % NT == 0 && NT % 32 == 0, "a-rows split evenly over the block");
   __shared__ float2 phc[N], php[N];

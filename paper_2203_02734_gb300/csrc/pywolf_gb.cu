@@ -858,8 +858,18 @@ cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::Pass
   cudaError_t e;
   // Without W (S and the P1 row only) the second pass is smu_from_v_kernel: two dot products per
   // column instead of the full DFT over point 1, reading V in its own layout.
+  // One wave of resident blocks, each taking the same number of column groups: blocks left for a
+  // second wave, or a last round of a few blocks, stream V at a fraction of the bandwidth.
   auto smu = [&](auto k, int groups, int nt) -> cudaError_t {
-    k<<<std::min(groups, num_sms() * (2048 / nt)), nt, 0, s>>>(b);
+    static int grid = 0;
+    if (grid == 0) {
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0);
+      if (e != cudaSuccess) return e;
+      const int resident = std::max(1, per_sm) * num_sms(), rounds = (groups + resident - 1) / resident;
+      grid = (groups + rounds - 1) / rounds;
+    }
+    k<<<grid, nt, 0, s>>>(b);
     return cudaGetLastError();
   };
   switch (N) {
