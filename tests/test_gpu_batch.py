@@ -246,15 +246,18 @@ def test_spectral_sum_on_common_grid():
 
 def test_batch_s_mu_only_pruned_pass():
     """Instances that keep no W take the pruned second pass (two dot products per column instead of
-    the DFT over point 1): N = 128 (register-resident pass A; separable GSM behind a lens, exact by
-    the per-axis quadrature), N = 64 with aperture and mask, N = 16 in the far field, each against
-    the FP64 oracle, sequenced mode, run twice."""
+    the DFT over point 1): N = 128 and 96 (register-resident pass A; separable GSM behind a lens,
+    exact by the per-axis quadrature), N = 64 with aperture and mask, N = 32 with aperture and mask
+    in the far field, N = 16 in the far field, each against the FP64 oracle, sequenced mode, run
+    twice.  Every size has its own grid of the S/mu pass (one wave of equal blocks)."""
     import torch
     import paper_2203_02734_gb300 as pw
     cases = [  # (N, z, farfield, lam, aperture, lens, with mask, P1)
         (128, 0.45, 0, 610e-9, 0.0, 0.35, False, (61, 66)),
         (64, 0.3, 0, 580e-9, 0.4e-3, 0.0, True, (30, 35)),
         (16, 0.7, 1, 633e-9, 0.0, 0.0, False, (7, 9)),
+        (96, 0.5, 0, 600e-9, 0.0, 0.4, False, (47, 50)),
+        (32, 0.6, 1, 620e-9, 0.25e-3, 0.0, True, (15, 17)),
     ]
     insts, outs, keep = [], [], []
     for k, (N, z, ff, lam, ap, lf, use_mask, P1) in enumerate(cases):
@@ -279,7 +282,7 @@ def test_batch_s_mu_only_pruned_pass():
         pw.pw_batch_check(b)
         torch.cuda.synchronize()
         for k, ((N, z, ff, lam, ap, lf, use_mask, P1), (S, mu, m)) in enumerate(zip(cases, outs)):
-            if N == 128:
+            if N in (96, 128):
                 ref = O.gsm_separable_quadrature(N, DXI, lam, z, 0.1e-3, 0.05e-3, 1.0 + 0.1 * k, lens_f=lf)
             else:
                 ref = _oracle(dict(N=N, z=z, ff=ff, lam=lam, ap=ap, lf=lf, mask=m, A=1.0 + 0.1 * k))
