@@ -849,6 +849,24 @@ pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
 
 // One propagation of a batched GSM instance on the single-instance kernels, from the instance's
 // tables: pass A, then pass B with S, the P1 row and, if b.W is set, the Hermitian W store.
+// The S / P1-row pass of an instance without W: one wave of resident blocks, each taking the same
+// number of column groups (blocks left for a second wave, or a last round of a few blocks, stream V
+// at a fraction of the bandwidth).  The grid is cached per N.
+template <int NN>
+cudaError_t launch_smu(const pw::PassBArgs& b, cudaStream_t s) {
+  static int grid = 0;
+  if (grid == 0) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pw::smu_from_v_kernel<NN>, pw::smu_nt<NN>(), 0);
+    if (e != cudaSuccess) return e;
+    const int groups = NN * NN / 4, resident = std::max(1, per_sm) * num_sms();
+    const int rounds = (groups + resident - 1) / resident;
+    grid = (groups + rounds - 1) / rounds;
+  }
+  pw::smu_from_v_kernel<NN><<<grid, pw::smu_nt<NN>(), 0, s>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
                                   const float2* Ein, const float2* mask, int ap_ithr, cudaStream_t s) {
   R128Extra x{};
@@ -858,25 +876,11 @@ cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::Pass
   cudaError_t e;
   // Without W (S and the P1 row only) the second pass is smu_from_v_kernel: two dot products per
   // column instead of the full DFT over point 1, reading V in its own layout.
-  // One wave of resident blocks, each taking the same number of column groups: blocks left for a
-  // second wave, or a last round of a few blocks, stream V at a fraction of the bandwidth.
-  auto smu = [&](auto k, int groups, int nt) -> cudaError_t {
-    static int grid = 0;
-    if (grid == 0) {
-      int per_sm = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0);
-      if (e != cudaSuccess) return e;
-      const int resident = std::max(1, per_sm) * num_sms(), rounds = (groups + resident - 1) / resident;
-      grid = (groups + rounds - 1) / rounds;
-    }
-    k<<<grid, nt, 0, s>>>(b);
-    return cudaGetLastError();
-  };
   switch (N) {
 #define PW_BCASE(NN)                                                                                        \
   case NN:                                                                                                  \
     if ((e = launch_a_mode<NN, pw::SRC_GSM>(vmap, a, x, s)) != cudaSuccess) return e;                       \
-    if (!b.W) return smu(pw::smu_from_v_kernel<NN>, NN * NN / 4, pw::smu_nt<NN>());                        \
+    if (!b.W) return launch_smu<NN>(b, s);                                                                  \
     if constexpr (NN == 128) return launch_b_r128<pw::W_HERM, true>(b, s);                                 \
     else if constexpr (NN == 96) return launch_b_r96<pw::W_HERM, true>(b, s);                              \
     else return launch_b<NN, pw::W_HERM, true>(b, s);
