@@ -175,8 +175,11 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     dft2d<8, 4, -1>(v);
-    if (lane == 0) bulk_wait_read_all();  // this warp's store of the previous slice has left buf
-    __syncthreads();
+    // Since the last block barrier of the previous slice each warp has touched only its own eight
+    // buffer rows (stage 3, the write-back, its TMA store), and exchange 1 writes only those rows:
+    // a warp barrier after the wait for the warp's own store is enough.
+    if (lane == 0) bulk_wait_read_all();  // this warp's store of the previous slice has left its rows
+    __syncwarp();
     float2 w3[2][4][4];
     stages_23<-1, true>(v, w3, buf, tw);
     __syncwarp();  // stage 3 read only the warp's own buffer rows 8 warp .. 8 warp + 7

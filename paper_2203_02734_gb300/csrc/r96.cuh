@@ -121,8 +121,6 @@ __global__ void __launch_bounds__(NT, 2)
   float2* X = smem;  // exchange buffer; the first N x N entries also stage the slice for TMA
   float2* tw = X + N * P;
   float2* ein = tw + N;
-  float* gA = reinterpret_cast<float*>(ein + N);
-  float* gB = gA + N;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int i = t; i < N; i += NT) {
     tw[i] = p.tw[i];
@@ -141,15 +139,11 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
       for (int kq = 0; kq < 3; ++kq)
         if (inside(warp + 6 * i + 12 * kp, lane + 32 * kq)) inmask |= 1ull << (i * 24 + kp * 3 + kq);
+  __syncthreads();  // tw, ein
+  // the GSM factors G(a, c), G(b, d) are read through L1 (no per-slice table, no barrier)
+  const float* __restrict__ G = p.G;
   for (int ab = blockIdx.x; ab < N * N; ab += gridDim.x) {
     const int a = ab / N, b = ab - a * N;
-    if (SRC == SRC_GSM) {
-      for (int i = t; i < N; i += NT) {
-        gA[i] = p.G[a * N + i];
-        gB[i] = p.G[b * N + i];
-      }
-    }
-    __syncthreads();
     float2 fab = inside(a, b) ? cmul(ein[a], ein[b]) : make_float2(0.f, 0.f);
     if (MASK) fab = cmul(fab, __ldg(mask + a * N + b));
     float2 s_ab = cconj(fab);
@@ -162,7 +156,7 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
     for (int kq = 0; kq < 3; ++kq) {
       const int d = lane + 32 * kq;
-      ed[kq] = SRC == SRC_GSM ? cscale(ein[d], gB[d]) : ein[d];
+      ed[kq] = SRC == SRC_GSM ? cscale(ein[d], __ldg(G + b * N + d)) : ein[d];
     }
     float2 v[2][8][3];
 #pragma unroll
@@ -170,7 +164,7 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
       for (int kp = 0; kp < 8; ++kp) {
         const int c = warp + 6 * i + 12 * kp;
-        const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], gA[c])) : cmul(s_ab, ein[c]);
+        const float2 sc = SRC == SRC_GSM ? cmul(s_ab, cscale(ein[c], __ldg(G + a * N + c))) : cmul(s_ab, ein[c]);
 #pragma unroll
         for (int kq = 0; kq < 3; ++kq) {
           const int d = lane + 32 * kq;
@@ -205,7 +199,7 @@ __global__ void __launch_bounds__(NT, 2)
   if (t == 0) bulk_wait_all();
 }
 
-constexpr size_t pass_a_smem() { return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2) + 2 * N * sizeof(float); }
+constexpr size_t pass_a_smem() { return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2); }
 constexpr size_t pass_b_smem() {
   return (size_t)N * P * sizeof(float2) + 2 * N * sizeof(float2) + 4 * 32 * sizeof(double);
 }

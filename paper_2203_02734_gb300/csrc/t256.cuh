@@ -201,8 +201,12 @@ __global__ void __launch_bounds__(NT1, 1) pass1_kernel(const __grid_constant__ C
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp) v[rp][rq] = cc[rp];
     }
-    if (lane == 0) bulk_wait_read_all();  // this warp's row stores of the previous tile have left buf
-    __syncthreads();  // tw (first tile); every read of buf of the previous tile is done
+    // Since the last block barrier of the previous tile each warp has touched only its own four
+    // buffer rows (stage 3, the write-back, its TMA store), and exchange 1 writes only those rows;
+    // tw is first read after the next block barrier.  A warp barrier after the wait for the warp's
+    // own store is enough.
+    if (lane == 0) bulk_wait_read_all();  // this warp's row stores of the previous tile have left its rows
+    __syncwarp();
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
