@@ -847,8 +847,6 @@ pw_status encode_vmap(CUtensorMap* map, void* work, int N) {
   return PW_OK;
 }
 
-// One propagation of a batched GSM instance on the single-instance kernels, from the instance's
-// tables: pass A, then pass B with S, the P1 row and, if b.W is set, the Hermitian W store.
 // The S / P1-row pass of an instance without W: one wave of resident blocks, each taking the same
 // number of column groups (blocks left for a second wave, or a last round of a few blocks, stream V
 // at a fraction of the bandwidth).  The grid is cached per N.
@@ -867,6 +865,8 @@ cudaError_t launch_smu(const pw::PassBArgs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One propagation of a batched GSM instance on the single-instance kernels, from the instance's
+// tables: pass A, then pass B with S, the P1 row and, if b.W is set, the Hermitian W store.
 cudaError_t launch_batch_instance(int N, const CUtensorMap& vmap, const pw::PassAArgs& a, const pw::PassBArgs& b,
                                   const float2* Ein, const float2* mask, int ap_ithr, cudaStream_t s) {
   R128Extra x{};
